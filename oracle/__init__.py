@@ -1,0 +1,257 @@
+"""FP64 CPU oracle for the 2DGS rasterizer -- TEST INFRASTRUCTURE ONLY.
+
+Only `tests/`, `__graft_entry__.smoke()` and `bench.py`'s CPU-baseline leg
+may import this package.  It wraps `splat2d_oracle.c` (plain C, FP64), which
+states the image-formation model of Sec. 3 (Eq. 1) with the 2DGS ray-splat
+intersection and its analytic gradient; see that file's header for the
+readings it takes.  Nothing here shares code with the CUDA library.
+
+Pinning: every function here is checked by `tests/test_oracle_pins.py`
+against closed forms, Eq. 1 in its screen-space form, an independent ray-
+plane intersection, invariants and FP64 central differences.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "splat2d_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libsplat2d_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NREC = 19
+ST_VISIBLE, ST_OPACITY, ST_NEAR, ST_EMPTY, ST_INVALID = 0, 1, 2, 3, 4
+SF_TILE_AMBIG, SF_NEAR_AMBIG, SF_PIX_AMBIG = 1, 2, 4
+PF_ALPHA_MIN, PF_T_MIN, PF_RECT, PF_NEAR, PF_ALPHA_MAX, PF_BRANCH = 1, 2, 4, 8, 16, 32
+# pixel flags that make a forward value legitimately differ between FP32 and FP64
+PF_FORWARD = PF_ALPHA_MIN | PF_T_MIN | PF_RECT | PF_NEAR
+
+
+def build(force: bool = False, openmp: bool = True) -> str:
+    """Compile the oracle with gcc into oracle/_lib (no fused multiply-add
+    contraction, so x86 and Arm give the same FP64 results)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_LIBDIR, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
+        cmds = ([base[:1] + ["-fopenmp"] + base[1:]] if openmp else []) + [base]
+        err = None
+        for cmd in cmds:
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode == 0:
+                os.replace(tmp, _LIB)
+                return _LIB
+            err = r.stderr
+        raise RuntimeError(f"oracle build failed:\n{err}")
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        i64 = ctypes.c_int64
+        lib.oracle_preprocess.argtypes = [i64] + [P] * 7 + [P] * 7
+        lib.oracle_render.argtypes = [ctypes.c_int, i64] + [P] * 8 + [P] * 5
+        lib.oracle_render_pixels.argtypes = [ctypes.c_int, i64] + [P] * 8 + [i64, P] + [P] * 4
+        lib.oracle_render_bwd.argtypes = [ctypes.c_int, i64] + [P] * 9 + [i64, P, P]
+        lib.oracle_chain.argtypes = [i64] + [P] * 12
+        lib.oracle_bin_sort.argtypes = [ctypes.c_int] + [P] * 9 + [i64]
+        lib.oracle_bin_sort.restype = i64
+        _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Config:
+    """Rasterizer constants (readings: alpha clamp 0.99, skip 1/255, stop
+    1e-4, low-pass sigma sqrt(1/2) px, near plane 0.01)."""
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    sigma_lp: float = 0.70710678118654752
+    z_near: float = 0.01
+    bg: tuple = (0.0, 0.0, 0.0)
+    tile_w: int = 16
+    tile_h: int = 16
+    # how close (relative / in pixels) a decision must be to be reported ambiguous
+    eps_alpha: float = 2e-5
+    eps_t: float = 2e-5
+    eps_px: float = 2e-5
+    eps_z: float = 1e-5
+
+    def array(self) -> np.ndarray:
+        f32 = lambda x: float(np.float32(x))  # the library receives FP32 constants
+        return np.array([f32(self.alpha_min), f32(self.alpha_max), f32(self.t_min), f32(self.sigma_lp),
+                         f32(self.z_near), f32(self.bg[0]), f32(self.bg[1]), f32(self.bg[2]),
+                         self.tile_w, self.tile_h, self.eps_alpha, self.eps_t, self.eps_px, self.eps_z],
+                        dtype=np.float64)
+
+
+def cam_array(view) -> np.ndarray:
+    Rt = np.asarray(view.Rt, np.float32).astype(np.float64)
+    f32 = lambda x: float(np.float32(x))
+    return np.concatenate([[view.width, view.height, f32(view.fx), f32(view.fy), f32(view.cx), f32(view.cy)],
+                           Rt.reshape(-1)]).astype(np.float64)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+@dataclass
+class Prep:
+    rec: np.ndarray       # (n, 19) float64
+    status: np.ndarray    # (n,) int32
+    pixrect: np.ndarray   # (n, 4) int32 inclusive x0 y0 x1 y1
+    tilerect: np.ndarray  # (n, 4) int32
+    amb: np.ndarray       # (n, 8) int32 widest / narrowest pixel rect
+    zbits: np.ndarray     # (n,) uint32
+    sflags: np.ndarray    # (n,) uint32
+    cam: np.ndarray
+    cfg: np.ndarray
+
+
+def preprocess(means, scales, quats, opacity, rgb, view, cfg: Config, cam: Optional[np.ndarray] = None) -> Prep:
+    """Per-surfel records of one view.  `cam` (W, H, fx, fy, cx, cy, Rt[12])
+    in FP64 overrides `view`, for finite differences of the pose."""
+    lib = _load()
+    means, scales, quats = _c(means, np.float32), _c(scales, np.float32), _c(quats, np.float32)
+    opacity, rgb = _c(opacity, np.float32), _c(rgb, np.float32)
+    n = means.shape[0]
+    rec = np.zeros((n, NREC)); status = np.zeros(n, np.int32)
+    pr = np.zeros((n, 4), np.int32); tr = np.zeros((n, 4), np.int32); amb = np.zeros((n, 8), np.int32)
+    zb = np.zeros(n, np.uint32); sf = np.zeros(n, np.uint32)
+    cam = cam_array(view) if cam is None else np.ascontiguousarray(cam, np.float64)
+    cf = cfg.array()
+    lib.oracle_preprocess(n, _p(means), _p(scales), _p(quats), _p(opacity), _p(rgb), _p(cam), _p(cf),
+                          _p(rec), _p(status), _p(pr), _p(tr), _p(amb), _p(zb), _p(sf))
+    return Prep(rec, status, pr, tr, amb, zb, sf, cam, cf)
+
+
+def preprocess_scene_view(scene, v: int, cfg: Config) -> Prep:
+    off, cnt = scene.view_ranges()[v]
+    sl = slice(off, off + cnt)
+    return preprocess(scene.means[sl], scene.scales[sl], scene.quats[sl], scene.opacity[sl],
+                      scene.rgb[sl], scene.views[v], cfg)
+
+
+@dataclass
+class Image:
+    out: np.ndarray     # (8, H, W): r, g, b, depth, nx, ny, nz, alpha
+    tfinal: np.ndarray  # (H, W)
+    nblend: np.ndarray  # (H, W)
+    pflags: np.ndarray  # (H, W) uint32
+    phash: np.ndarray   # (H, W) uint64 decision signature
+
+    @property
+    def rgb(self):
+        return self.out[0:3]
+
+    @property
+    def depth(self):
+        return self.out[3]
+
+    @property
+    def normal(self):
+        return self.out[4:7]
+
+    @property
+    def alpha(self):
+        return self.out[7]
+
+
+def render(prep: Prep, mode: int = 1) -> Image:
+    """mode 0: definition (every surfel at every pixel); mode 1: binned."""
+    lib = _load()
+    W, H = int(prep.cam[0]), int(prep.cam[1])
+    n = prep.rec.shape[0]
+    out = np.zeros((8, H, W)); tf = np.zeros((H, W)); nb = np.zeros((H, W), np.int32)
+    pf = np.zeros((H, W), np.uint32); ph = np.zeros((H, W), np.uint64)
+    lib.oracle_render(mode, n, _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb), _p(prep.zbits),
+                      _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(out), _p(tf), _p(nb), _p(pf), _p(ph))
+    return Image(out, tf, nb, pf, ph)
+
+
+def render_pixels(prep: Prep, pix: np.ndarray, mode: int = 1):
+    """Outputs (8, npix), tfinal, nblend, pflags at the listed flat pixel indices."""
+    lib = _load()
+    pix = _c(pix, np.int64)
+    m = pix.shape[0]
+    out = np.zeros((8, m)); tf = np.zeros(m); nb = np.zeros(m, np.int32); pf = np.zeros(m, np.uint32)
+    lib.oracle_render_pixels(mode, prep.rec.shape[0], _p(prep.rec), _p(prep.status), _p(prep.pixrect),
+                             _p(prep.amb), _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), m,
+                             _p(pix), _p(out), _p(tf), _p(nb), _p(pf))
+    return out, tf, nb, pf
+
+
+@dataclass
+class Grads:
+    means: np.ndarray
+    scales: np.ndarray
+    quats: np.ndarray
+    opacity: np.ndarray
+    rgb: np.ndarray
+    pose: np.ndarray  # (6,) d rho, d phi
+
+
+def render_bwd(means, scales, quats, prep: Prep, g8: np.ndarray, mode: int = 1,
+               pix: Optional[np.ndarray] = None, grads: Optional[Grads] = None) -> Grads:
+    """Gradients of sum(g8 * outputs) for one view; accumulated into `grads`."""
+    lib = _load()
+    means, scales, quats = _c(means, np.float32), _c(scales, np.float32), _c(quats, np.float32)
+    n = prep.rec.shape[0]
+    g8 = _c(g8, np.float64)
+    grec = np.zeros((n, NREC))
+    if pix is None:
+        lib.oracle_render_bwd(mode, n, _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb),
+                              _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(g8), -1, None,
+                              _p(grec))
+    else:
+        pix = _c(pix, np.int64)
+        lib.oracle_render_bwd(mode, n, _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb),
+                              _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(g8),
+                              pix.shape[0], _p(pix), _p(grec))
+    if grads is None:
+        grads = Grads(np.zeros((n, 3)), np.zeros((n, 2)), np.zeros((n, 4)), np.zeros(n), np.zeros((n, 3)),
+                      np.zeros(6))
+    lib.oracle_chain(n, _p(means), _p(scales), _p(quats), _p(prep.status), _p(prep.cam), _p(grec),
+                     _p(grads.means), _p(grads.scales), _p(grads.quats), _p(grads.opacity), _p(grads.rgb),
+                     _p(grads.pose))
+    grads.grec = grec
+    return grads
+
+
+def bin_sort(preps, tile_bases, tiles_x, surfel_offsets, cap: Optional[int] = None):
+    """Keys and values of every view's instances, stably sorted by key."""
+    lib = _load()
+    counts = np.array([p.rec.shape[0] for p in preps], np.int64)
+    status = np.concatenate([p.status for p in preps]).astype(np.int32)
+    tr = np.concatenate([p.tilerect for p in preps]).astype(np.int32)
+    zb = np.concatenate([p.zbits for p in preps]).astype(np.uint32)
+    sidx = np.concatenate([np.arange(c, dtype=np.int64) + o for c, o in zip(counts, surfel_offsets)])
+    tb = np.asarray(tile_bases, np.int64)
+    tx = np.asarray(tiles_x, np.int32)
+    need = lib.oracle_bin_sort(len(preps), _p(counts), _p(status), _p(tr), _p(zb), _p(sidx), _p(tb), _p(tx),
+                               None, None, 0)
+    keys = np.zeros(max(need, 1), np.uint64)
+    vals = np.zeros(max(need, 1), np.uint32)
+    lib.oracle_bin_sort(len(preps), _p(counts), _p(status), _p(tr), _p(zb), _p(sidx), _p(tb), _p(tx),
+                        _p(keys), _p(vals), need)
+    return keys[:need], vals[:need]

@@ -1,0 +1,45 @@
+"""Sensitivity of the oracle pins: plant one plausible mistake at a time in a
+copy of the oracle (on the CPU, in a temporary directory) and check that the
+pin suite fails for every one of them."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# (name, original text, planted mistake)
+MUTATIONS = [
+    ("rotation sign", "R[1] = 2 * (x * y - w * z)", "R[1] = 2 * (x * y + w * z)"),
+    ("rotation jacobian entry", "{2 * z, 2 * y, 2 * x, 2 * w}", "{2 * z, 2 * y, 2 * x, -2 * w}"),
+    ("adjugate vjp sign", "dM[r0 * 3 + c1] -= g * M[r1 * 3 + c0];", "dM[r0 * 3 + c1] += g * M[r1 * 3 + c0];"),
+    ("background dropped in reverse pass",
+     "double SC[3] = {tf * cfg.bg[0], tf * cfg.bg[1], tf * cfg.bg[2]}", "double SC[3] = {0, 0, 0}"),
+    ("alpha-output term", "da += dA * tf / om;", "da += dA * tf;"),
+    ("center gradient term", "dM[8] -= (gr[R_CX] * g.M[2] + gr[R_CY] * g.M[5]) / (m22 * m22);",
+     "dM[8] -= (gr[R_CX] * g.M[2]) / (m22 * m22);"),
+    ("pose cross order", "cross(g.nc, dnc, cr);", "cross(dnc, g.nc, cr);"),
+    ("normal not turned to camera", "g->flip = (d > 0) ? -1.0 : 1.0;", "g->flip = 1.0;"),
+    ("stop rule", "if (Tn < cfg->t_min) break;", "if (Tn < 0.5 * cfg->t_min) break;"),
+    ("low-pass width", "(dx * dx + dy * dy) / (cfg->sigma_lp * cfg->sigma_lp)",
+     "(dx * dx + dy * dy) / (2 * cfg->sigma_lp * cfg->sigma_lp)"),
+    ("rect too small", "double lo = fmin(fmin(r1, r2), c0 - rlp)", "double lo = fmin(fmin(r1, r2), c0 - rlp) + 0.3"),
+    ("opacity-aware extent", "double k2 = 2.0 * log(op / cfg.alpha_min);", "double k2 = 1.5 * log(op / cfg.alpha_min);"),
+    ("homogeneous divide gradient", "dcc = -(b->e.u * du + b->e.v * dv) / c;", "dcc = -(b->e.u * du - b->e.v * dv) / c;"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,orig,bad", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(tmp_path, name, orig, bad):
+    src = open(os.path.join(ROOT, "oracle", "splat2d_oracle.c")).read()
+    assert orig in src, f"mutation anchor for {name!r} no longer in the oracle"
+    for d in ("oracle", "tests", "paper_2604_03092_gb300"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("_lib", "__pycache__", "golden"))
+    (tmp_path / "oracle" / "splat2d_oracle.c").write_text(src.replace(orig, bad))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
