@@ -1,0 +1,243 @@
+/*
+ * splat2d.h -- C ABI of the GB300 (sm_103a) differentiable 2D Gaussian surfel
+ * rasterizer: the data-parallel hot path of Flash-Mono's mapping backend.
+ *
+ * What is rendered (Sec. 3, Eq. 1 and the 2DGS surfel primitive it adopts):
+ * each surfel i has a center mu_i, colour c_i, opacity sigma_i, rotation r_i
+ * (a quaternion) and two tangent scales s_i.  Seen from a pinhole camera
+ * (intrinsics fx, fy, cx, cy; world-to-camera pose [R|t]) the ray through a
+ * pixel meets the surfel plane at local coordinates (u, v) (ray-splat
+ * intersection); the surfel's weight there is
+ *     w_i = min(alpha_max, sigma_i * max(exp(-(u^2+v^2)/2),
+ *                                        exp(-|x - c_i|^2 / (2 lowpass^2))))
+ * (object-space / screen-space low-pass max, c_i the projected center), and
+ * the pixel's colour, depth and accumulated alpha are, front to back in
+ * depth order,
+ *     (I, D, A) = sum_i (c_i, z_i, 1) w_i prod_{j<i} (1 - w_j)     (Eq. 1)
+ * with z_i the depth of the surfel center along the optical axis, plus a
+ * camera-frame normal N = sum_i n_i w_i prod_{j<i}(1 - w_j).  Pairs with
+ * w_i < alpha_min are skipped, and a pixel stops before the first surfel that
+ * would take its transmittance below t_min.  I also gets T_final * bg.
+ *
+ * The backward pass gives dL/d(means, scales, quats, opacity, rgb) and, per
+ * view, dL/dxi for the left perturbation T_cw <- Exp(xi) T_cw, xi = (rho,
+ * phi), evaluated at xi = 0 (the camera se(3) tangent used when refining
+ * poses).
+ *
+ * Conventions for every call:
+ *  - Host pointers: the splat2d_config, splat2d_problem (and its view array),
+ *    splat2d_surfels and splat2d_grads structs themselves.  Device pointers:
+ *    the arrays they point to, the workspace and every image buffer.
+ *  - The caller owns all memory.  The library never allocates device memory:
+ *    the caller allocates a workspace of splat2d_workspace_size() bytes
+ *    (256-byte aligned) and passes the same problem to every call.
+ *  - Calls are asynchronous on `stream`, make no host synchronisation and no
+ *    allocation, and are capturable in a CUDA graph (except
+ *    splat2d_status / splat2d_stats, which synchronise).
+ *  - Return value: SPLAT2D_OK or a negative error code for a problem found on
+ *    the host (bad argument, workspace too small, CUDA launch error).
+ *    Conditions found on the device (instance capacity exceeded, a bounded
+ *    wait that gave up) are recorded in the workspace and read with
+ *    splat2d_status() after the stream is synchronised.
+ *  - Layouts: FP32 everywhere.  Surfel arrays are row-major [N, k].  Images
+ *    are planar and packed per view: view v's RGB and normal occupy
+ *    [3][H_v][W_v] at element offset 3*pixel_offset_v of their buffers, and
+ *    its depth and alpha occupy [H_v][W_v] at pixel_offset_v.  Pixel (i, j)
+ *    is sampled at (i + 0.5, j + 0.5).
+ */
+#ifndef SPLAT2D_H
+#define SPLAT2D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t (0 = legacy default stream). */
+typedef struct CUstream_st* splat2d_stream;
+
+enum {
+  SPLAT2D_OK = 0,
+  SPLAT2D_ERR_INVALID_ARG = -1,        /* a host-side argument is out of range */
+  SPLAT2D_ERR_WORKSPACE_TOO_SMALL = -2,
+  SPLAT2D_ERR_CUDA = -3,               /* a CUDA launch or copy failed */
+  SPLAT2D_ERR_CAPACITY = -4,           /* device: more tile instances than instance_capacity */
+  SPLAT2D_ERR_TIMEOUT = -5,            /* device: a bounded wait gave up */
+  SPLAT2D_ERR_NO_DEVICE = -6
+};
+
+/* One camera and the surfel range it renders. */
+typedef struct {
+  int32_t width, height;        /* pixels, 1..32768 */
+  float fx, fy, cx, cy;         /* pinhole intrinsics, pixels */
+  float Rt[12];                 /* world -> camera [R | t], row-major 3x4 */
+  int64_t surfel_offset;        /* first surfel of the range this view renders */
+  int64_t surfel_count;         /* number of surfels in the range */
+  int64_t pixel_offset;         /* start of this view's pixels in the packed images */
+} splat2d_view;
+
+/* Surfel parameters (device arrays, FP32, row-major). */
+typedef struct {
+  const float* means;    /* [N, 3] world centers */
+  const float* scales;   /* [N, 2] tangent scales (linear) */
+  const float* quats;    /* [N, 4] rotation (w, x, y, z), any nonzero norm: normalised inside */
+  const float* opacity;  /* [N] in [0, 1] (linear) */
+  const float* rgb;      /* [N, 3] colour */
+  int64_t n;
+} splat2d_surfels;
+
+/* Gradient outputs (device arrays).  Accumulated into (+=): zero them first.
+ * Any pointer may be NULL to skip that output. */
+typedef struct {
+  float* means;    /* [N, 3] */
+  float* scales;   /* [N, 2] */
+  float* quats;    /* [N, 4] */
+  float* opacity;  /* [N] */
+  float* rgb;      /* [N, 3] */
+  float* pose;     /* [n_views, 6]: dL/d(rho_xyz, phi_xyz) */
+} splat2d_grads;
+
+/* Rasterizer constants.  Defaults (splat2d_default_config): 16x16 tiles,
+ * chunk 256, alpha in [1/255, 0.99], t_min 1e-4, lowpass sqrt(1/2) px,
+ * z_near 0.01, black background. */
+typedef struct {
+  int32_t tile_w, tile_h;   /* one of 8x8, 16x16, 32x8 */
+  int32_t chunk;            /* surfels staged per shared-memory batch: 64, 128 or 256 */
+  float alpha_min;          /* skip pairs with alpha below this */
+  float alpha_max;          /* clamp of alpha (keeps the reverse pass finite) */
+  float t_min;              /* stop a pixel before T would drop below this */
+  float lowpass_sigma;      /* screen-space low-pass std-dev in pixels (0 = off) */
+  float z_near;             /* cull surfels whose opacity-aware disk reaches z <= z_near */
+  float bg[3];              /* background colour added as T_final * bg */
+  uint32_t flags;           /* SPLAT2D_FLAG_* */
+} splat2d_config;
+
+/* flags */
+#define SPLAT2D_FLAG_NO_STATS 1u   /* skip the pair counters (kept by default) */
+
+/* The shape of one problem: the views (host array) and sizes.  Pass the same
+ * problem (same values) to every call that uses one workspace. */
+typedef struct {
+  const splat2d_view* views;   /* host array of n_views */
+  int32_t n_views;             /* 1..4096 */
+  int64_t n_surfels;           /* size of the surfel arrays */
+  int64_t instance_capacity;   /* max (tile, surfel) instances per iteration */
+} splat2d_problem;
+
+/* Device-side counters of the last iteration (see splat2d_stats). */
+typedef struct {
+  int64_t status;              /* SPLAT2D_OK or a device error code */
+  int64_t needed_capacity;     /* instances the last binning needed */
+  int64_t n_instances;         /* instances binned and sorted */
+  int64_t n_visible;           /* visible (view, surfel) pairs */
+  int64_t fwd_pairs_evaluated; /* (pixel, surfel) pairs whose alpha the forward computed */
+  int64_t fwd_pairs_blended;   /* ... of which blended */
+  int64_t bwd_pairs_evaluated; /* (pixel, surfel) pairs the reverse pass recomputed */
+  int64_t bwd_pairs_blended;   /* ... of which carried gradient */
+  int64_t sort_passes;         /* radix passes run */
+  int64_t reserved[7];
+} splat2d_stats_t;
+
+/* Fill `cfg` with the defaults above. */
+void splat2d_default_config(splat2d_config* cfg);
+
+/* Bytes of workspace the problem needs (0 if the arguments are invalid).
+ * The workspace holds, per (view, surfel) pair of every view's range, an
+ * 80-byte render record and a 64-byte gradient record, plus 24 bytes per
+ * unit of instance_capacity and 16 bytes per pixel. */
+size_t splat2d_workspace_size(const splat2d_config* cfg, const splat2d_problem* prob);
+
+/*
+ * Per-surfel preprocess (one launch over every view's surfel range): camera
+ * transform, tangent frame from the normalised quaternion, the ray-splat
+ * intersection transform, projected center, depth key, camera normal turned
+ * to face the camera, culls, and the opacity-aware screen extent united with
+ * the low-pass square, as a pixel rect.  Writes render records into `ws` and
+ * resets the device status.  Returns SPLAT2D_ERR_INVALID_ARG for a bad
+ * problem or surfel count mismatch, SPLAT2D_ERR_WORKSPACE_TOO_SMALL if
+ * ws_bytes < splat2d_workspace_size().
+ */
+int splat2d_preprocess(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                       void* ws, size_t ws_bytes, splat2d_stream stream);
+
+/*
+ * Tile binning and sort: every visible (view, surfel) pair emits one
+ * instance per tile of its rect, key = (global tile) << 32 | FP32 depth bits,
+ * value = surfel index; a device LSD radix sort orders them by key, stable
+ * (equal keys keep ascending surfel index); then each tile's [start, end)
+ * range is found.  If the instances exceed instance_capacity the device
+ * status becomes SPLAT2D_ERR_CAPACITY with the needed count and nothing is
+ * rendered; re-run with a larger capacity.
+ */
+int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                     splat2d_stream stream);
+
+/*
+ * Forward compositing: one persistent launch over every (view, tile); each
+ * tile stages chunks of its sorted surfels in shared memory and composites
+ * front to back with warp-level early termination.  Writes rgb, depth,
+ * normal, alpha (packed per view as described above; any may be NULL) and
+ * keeps per-pixel T_final and the last blended index in `ws` for the
+ * backward pass.
+ */
+int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                       float* rgb, float* depth, float* normal, float* alpha, splat2d_stream stream);
+
+/*
+ * Reverse pass: walks each pixel back to front from its last blended surfel,
+ * recovering the transmittance by division instead of storing per-pixel
+ * lists; per-surfel gradients are summed across each warp with shuffles and
+ * across the tile in shared memory before one vector atomic per (tile,
+ * surfel); then a per-surfel pass chains them to the parameters and reduces
+ * the per-view pose tangent.  d_* are upstream gradients laid out like the
+ * forward outputs (NULL = zero).  Must follow splat2d_render_fwd on the same
+ * workspace with unchanged surfels.
+ */
+int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                       void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth,
+                       const float* d_normal, const float* d_alpha, const splat2d_grads* grads,
+                       splat2d_stream stream);
+
+/* Synchronise `stream`, read the device status and counters of the last
+ * iteration into *out.  Returns out->status (or a host error). */
+int splat2d_stats(const void* ws, splat2d_stats_t* out, splat2d_stream stream);
+
+/* Like splat2d_stats but returns only the status and, if needed_capacity is
+ * not NULL, the instance count the last binning needed. */
+int splat2d_status(const void* ws, int64_t* needed_capacity, splat2d_stream stream);
+
+/* Byte offsets of the workspace sub-buffers (for inspection and tests). */
+typedef struct {
+  size_t records;     /* [R] 80-byte render records, R = sum of view ranges */
+  size_t ntiles;      /* [R] uint32 tile count per record (0 = culled) */
+  size_t keys;        /* [capacity] uint64 sorted keys (after splat2d_bin_sort) */
+  size_t vals;        /* [capacity] uint32 sorted surfel indices */
+  size_t ranges;      /* [T] uint32 x2 per global tile: [start, end) */
+  size_t tfinal;      /* [P] float per pixel */
+  size_t last;        /* [P] uint32 per pixel: one past the last blended entry of its tile list */
+  size_t total;       /* = splat2d_workspace_size */
+  int64_t n_records;  /* R */
+  int64_t n_tiles;    /* T */
+  int64_t n_pixels;   /* P */
+} splat2d_layout;
+int splat2d_workspace_layout(const splat2d_config* cfg, const splat2d_problem* prob, splat2d_layout* out);
+
+/*
+ * The radix sort on its own: stably sorts n (key, value) pairs in place by
+ * the low `key_bits` bits of the keys (1..64; higher bits must be zero).
+ * keys/vals are device arrays; tmp is a device buffer of
+ * splat2d_sort_tmp_size(n) bytes.  Asynchronous on `stream`.
+ */
+size_t splat2d_sort_tmp_size(int64_t n);
+int splat2d_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits, void* tmp, size_t tmp_bytes,
+                       splat2d_stream stream);
+
+/* Human-readable name of a status code. */
+const char* splat2d_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLAT2D_H */

@@ -1,0 +1,386 @@
+// C ABI of libsplat2d: argument checks, workspace layout and the launch
+// sequence of each call.  See include/splat2d.h for the contract.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "splat2d_internal.cuh"
+
+namespace s2d {
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cached[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 1;
+  }
+  return cached[dev];
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static bool valid_config(const splat2d_config* c) {
+  if (!c) return false;
+  const bool tile_ok = (c->tile_w == 16 && c->tile_h == 16) || (c->tile_w == 8 && c->tile_h == 8) ||
+                       (c->tile_w == 32 && c->tile_h == 8);
+  const bool chunk_ok = c->chunk == 64 || c->chunk == 128 || c->chunk == 256;
+  if (!tile_ok || !chunk_ok) return false;
+  if (!(c->alpha_min > 0.f && c->alpha_min < 1.f)) return false;
+  if (!(c->alpha_max >= c->alpha_min && c->alpha_max < 1.f)) return false;
+  if (!(c->t_min > 0.f && c->t_min < 1.f)) return false;
+  if (!(c->lowpass_sigma >= 0.f && std::isfinite(c->lowpass_sigma))) return false;
+  if (!(c->z_near > 0.f && std::isfinite(c->z_near))) return false;
+  return true;
+}
+
+// Number of key bits in use: 32 depth bits + bits of the largest tile index.
+static int key_bits_for(int64_t T) {
+  int b = 0;
+  while (b < 40 && (int64_t(1) << b) < T) b++;
+  return 32 + b;
+}
+
+struct HostTables {
+  std::vector<DView> views;
+  std::vector<DGroup> groups;
+};
+
+static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob, Layout* L, HostTables* H) {
+  if (!cfg || !prob || !prob->views || prob->n_views < 1 || prob->n_views > 4096) return false;
+  if (prob->n_surfels < 0 || prob->n_surfels > 0xffffffffll) return false;
+  if (prob->instance_capacity < 0 || prob->instance_capacity > 0xffffffffll) return false;
+  const int V = prob->n_views;
+  if (H) {
+    H->views.assign(V, DView{});
+    H->groups.clear();
+  }
+  int64_t R = 0, T = 0, P = 0, work = 0;
+  int G = 0;
+  std::vector<std::pair<int64_t, int64_t>> ranges;
+  for (int v = 0; v < V; v++) {
+    const splat2d_view& sv = prob->views[v];
+    if (sv.width < 1 || sv.height < 1 || sv.width > 32768 || sv.height > 32768) return false;
+    if (!(sv.fx > 0.f) || !(sv.fy > 0.f) || !std::isfinite(sv.cx) || !std::isfinite(sv.cy)) return false;
+    for (int k = 0; k < 12; k++)
+      if (!std::isfinite(sv.Rt[k])) return false;
+    if (sv.surfel_offset < 0 || sv.surfel_count < 0 || sv.surfel_offset + sv.surfel_count > prob->n_surfels)
+      return false;
+    if (sv.pixel_offset < 0) return false;
+    const int tx = (sv.width + cfg->tile_w - 1) / cfg->tile_w;
+    const int ty = (sv.height + cfg->tile_h - 1) / cfg->tile_h;
+    const bool new_group = v == 0 || sv.surfel_offset != prob->views[v - 1].surfel_offset ||
+                           sv.surfel_count != prob->views[v - 1].surfel_count;
+    if (new_group) {
+      if (H) {
+        DGroup g;
+        g.soff = sv.surfel_offset;
+        g.scnt = sv.surfel_count;
+        g.wbase = work;
+        g.v0 = v;
+        g.v1 = v + 1;
+        H->groups.push_back(g);
+      }
+      ranges.push_back({sv.surfel_offset, sv.surfel_offset + sv.surfel_count});
+      work += sv.surfel_count;
+      G++;
+    } else if (H) {
+      H->groups.back().v1 = v + 1;
+    }
+    if (H) {
+      DView& d = H->views[v];
+      d.W = sv.width;
+      d.H = sv.height;
+      d.fx = sv.fx; d.fy = sv.fy; d.cx = sv.cx; d.cy = sv.cy;
+      for (int r = 0; r < 3; r++) {
+        for (int c = 0; c < 3; c++) d.R[r * 3 + c] = sv.Rt[r * 4 + c];
+        d.t[r] = sv.Rt[r * 4 + 3];
+      }
+      d.soff = sv.surfel_offset;
+      d.scnt = sv.surfel_count;
+      d.poff = sv.pixel_offset;
+      d.rbase = R;
+      d.tile_base = (int32_t)T;
+      d.tiles_x = tx;
+      d.tiles_y = ty;
+      d.group = G - 1;
+    }
+    R += sv.surfel_count;
+    T += (int64_t)tx * ty;
+    P = std::max<int64_t>(P, sv.pixel_offset + (int64_t)sv.width * sv.height);
+  }
+  if (R > 0xffffffffll || T > 0x7fffffffll) return false;
+  std::sort(ranges.begin(), ranges.end());
+  bool overlap = false;
+  for (size_t i = 1; i < ranges.size(); i++)
+    if (ranges[i].first < ranges[i - 1].second) overlap = true;
+
+  L->V = V;
+  L->G = G;
+  L->R = R;
+  L->T = T;
+  L->P = P;
+  L->cap = prob->instance_capacity;
+  L->n_work = work;
+  L->groups_overlap = overlap;
+  L->n_scan_tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
+  L->sort_blocks = std::min(SORT_MAX_BLOCKS, 4 * sm_count());
+  L->key_bits = key_bits_for(T);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  L->header = take(256);
+  L->views = take(sizeof(DView) * V);
+  L->groups = take(sizeof(DGroup) * G);
+  L->ntiles = take(sizeof(uint32_t) * R);
+  L->records = take(sizeof(float4) * REC_F4 * R);
+  L->rgrad = take(sizeof(float) * GRAD_F * R);
+  L->scan_part = take(sizeof(unsigned long long) * (L->n_scan_tiles + 1));
+  L->keys0 = take(sizeof(uint64_t) * L->cap);
+  L->keys1 = take(sizeof(uint64_t) * L->cap);
+  L->vals0 = take(sizeof(uint32_t) * L->cap);
+  L->vals1 = take(sizeof(uint32_t) * L->cap);
+  L->sort_hist = take(sizeof(uint32_t) * (256 * (size_t)L->sort_blocks + 256));
+  L->ranges = take(sizeof(uint2) * T);
+  L->tile_order = take(sizeof(uint32_t) * T);
+  L->tile_hist = take(sizeof(uint32_t) * ORDER_BINS);
+  L->tfinal = take(sizeof(float) * P);
+  L->last = take(sizeof(uint32_t) * P);
+  L->total = off;
+  return true;
+}
+
+bool compute_layout(const splat2d_config* cfg, const splat2d_problem* prob, Layout* L) {
+  if (!valid_config(cfg)) return false;
+  return build_tables(cfg, prob, L, nullptr);
+}
+
+static RastParams make_params(const splat2d_config* c) {
+  RastParams P;
+  P.alpha_min = c->alpha_min;
+  P.alpha_max = c->alpha_max;
+  P.t_min = c->t_min;
+  P.z_near = c->z_near;
+  P.lp_r = c->lowpass_sigma;
+  P.lp_scale = c->lowpass_sigma > 0.f ? kLog2e / (2.f * c->lowpass_sigma * c->lowpass_sigma) : 1e30f;
+  P.bg[0] = c->bg[0]; P.bg[1] = c->bg[1]; P.bg[2] = c->bg[2];
+  P.tile_w = c->tile_w;
+  P.tile_h = c->tile_h;
+  P.stats = (c->flags & SPLAT2D_FLAG_NO_STATS) ? 0 : 1;
+  return P;
+}
+
+static int check_common(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                        Layout* L) {
+  if (!valid_config(cfg)) return SPLAT2D_ERR_INVALID_ARG;
+  if (!build_tables(cfg, prob, L, nullptr)) return SPLAT2D_ERR_INVALID_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return SPLAT2D_ERR_INVALID_ARG;
+  if (ws_bytes < L->total) return SPLAT2D_ERR_WORKSPACE_TOO_SMALL;
+  return SPLAT2D_OK;
+}
+
+static int final_sorted_buffer(const Layout& L) { return ((L.key_bits + 7) / 8) & 1; }
+
+}  // namespace s2d
+
+using namespace s2d;
+
+extern "C" {
+
+void splat2d_default_config(splat2d_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->tile_w = 16;
+  c->tile_h = 16;
+  c->chunk = 256;
+  c->alpha_min = 1.0f / 255.0f;
+  c->alpha_max = 0.99f;
+  c->t_min = 1e-4f;
+  c->lowpass_sigma = 0.70710678118654752f;
+  c->z_near = 0.01f;
+}
+
+size_t splat2d_workspace_size(const splat2d_config* cfg, const splat2d_problem* prob) {
+  Layout L;
+  if (!compute_layout(cfg, prob, &L)) return 0;
+  return L.total;
+}
+
+int splat2d_workspace_layout(const splat2d_config* cfg, const splat2d_problem* prob, splat2d_layout* out) {
+  Layout L;
+  if (!out || !compute_layout(cfg, prob, &L)) return SPLAT2D_ERR_INVALID_ARG;
+  const int fb = final_sorted_buffer(L);
+  out->records = L.records;
+  out->ntiles = L.ntiles;
+  out->keys = fb ? L.keys1 : L.keys0;
+  out->vals = fb ? L.vals1 : L.vals0;
+  out->ranges = L.ranges;
+  out->tfinal = L.tfinal;
+  out->last = L.last;
+  out->total = L.total;
+  out->n_records = L.R;
+  out->n_tiles = L.T;
+  out->n_pixels = L.P;
+  return SPLAT2D_OK;
+}
+
+int splat2d_preprocess(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                       void* ws, size_t ws_bytes, splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  if (!surfels || surfels->n != prob->n_surfels) return SPLAT2D_ERR_INVALID_ARG;
+  if (prob->n_surfels > 0 && (!surfels->means || !surfels->scales || !surfels->quats || !surfels->opacity ||
+                              !surfels->rgb))
+    return SPLAT2D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(surfels->quats) & 15) return SPLAT2D_ERR_INVALID_ARG;
+  HostTables H;
+  build_tables(cfg, prob, &L, &H);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  if (cudaMemsetAsync(w + L.header, 0, 256, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  if (launch_upload(H.views.data(), sizeof(DView) * H.views.size(), w + L.views, st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  if (!H.groups.empty() &&
+      launch_upload(H.groups.data(), sizeof(DGroup) * H.groups.size(), w + L.groups, st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  RastParams P = make_params(cfg);
+  if (launch_preprocess(surfels, L, P, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                     splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  RastParams P = make_params(cfg);
+  Header* hdr = reinterpret_cast<Header*>(w + L.header);
+  if (launch_bin(L, P, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  int fb = 0;
+  if (cudaMemsetAsync(w + L.sort_hist + sizeof(uint32_t) * 256 * (size_t)L.sort_blocks, 0, 256 * sizeof(uint32_t),
+                      st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  if (launch_sort(reinterpret_cast<uint64_t*>(w + L.keys0), reinterpret_cast<uint32_t*>(w + L.vals0),
+                  reinterpret_cast<uint64_t*>(w + L.keys1), reinterpret_cast<uint32_t*>(w + L.vals1), &hdr->n_inst,
+                  L.cap, L.key_bits, reinterpret_cast<uint32_t*>(w + L.sort_hist), L.sort_blocks, &fb,
+                  st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  if (L.cap > 0 && fb != final_sorted_buffer(L)) return SPLAT2D_ERR_CUDA;
+  const uint64_t* keys = reinterpret_cast<const uint64_t*>(w + (final_sorted_buffer(L) ? L.keys1 : L.keys0));
+  if (launch_ranges(L, keys, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                       float* rgb, float* depth, float* normal, float* alpha, splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
+  if (launch_render_fwd(L, make_params(cfg), cfg->chunk, w, vals, rgb, depth, normal, alpha, st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                       void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
+                       const float* d_alpha, const splat2d_grads* grads, splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  if (!surfels || surfels->n != prob->n_surfels || !grads) return SPLAT2D_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const RastParams P = make_params(cfg);
+  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
+  if (launch_render_bwd(L, P, cfg->chunk, w, vals, d_rgb, d_depth, d_normal, d_alpha, st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  if (launch_preprocess_bwd(surfels, L, P, w, grads, L.groups_overlap, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_stats(const void* ws, splat2d_stats_t* out, splat2d_stream stream) {
+  if (!ws || !out) return SPLAT2D_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  Header h;
+  if (cudaMemcpy(&h, ws, sizeof(Header), cudaMemcpyDeviceToHost) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  out->status = h.status;
+  out->needed_capacity = (int64_t)h.needed;
+  out->n_instances = (int64_t)h.n_inst;
+  out->n_visible = (int64_t)h.n_visible;
+  out->fwd_pairs_evaluated = (int64_t)h.stat[STAT_FWD_EVAL];
+  out->fwd_pairs_blended = (int64_t)h.stat[STAT_FWD_BLEND];
+  out->bwd_pairs_evaluated = (int64_t)h.stat[STAT_BWD_EVAL];
+  out->bwd_pairs_blended = (int64_t)h.stat[STAT_BWD_BLEND];
+  return h.status;
+}
+
+int splat2d_status(const void* ws, int64_t* needed_capacity, splat2d_stream stream) {
+  splat2d_stats_t s;
+  int rc = splat2d_stats(ws, &s, stream);
+  if (rc == SPLAT2D_ERR_INVALID_ARG || rc == SPLAT2D_ERR_CUDA) return rc;
+  if (needed_capacity) *needed_capacity = s.needed_capacity;
+  return (int)s.status;
+}
+
+size_t splat2d_sort_tmp_size(int64_t n) {
+  if (n < 0) return 0;
+  return align256(sizeof(uint64_t) * (size_t)n) + align256(sizeof(uint32_t) * (size_t)n) +
+         align256(sizeof(uint32_t) * (256 * (size_t)std::min(SORT_MAX_BLOCKS, 4 * sm_count()) + 256));
+}
+
+int splat2d_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits, void* tmp, size_t tmp_bytes,
+                       splat2d_stream stream) {
+  if (n < 0 || n > 0xffffffffll || key_bits < 1 || key_bits > 64) return SPLAT2D_ERR_INVALID_ARG;
+  if (n == 0) return SPLAT2D_OK;
+  if (!keys || !vals || !tmp || (reinterpret_cast<uintptr_t>(tmp) & 255)) return SPLAT2D_ERR_INVALID_ARG;
+  if (tmp_bytes < splat2d_sort_tmp_size(n)) return SPLAT2D_ERR_WORKSPACE_TOO_SMALL;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* t = static_cast<char*>(tmp);
+  uint64_t* k1 = reinterpret_cast<uint64_t*>(t);
+  uint32_t* v1 = reinterpret_cast<uint32_t*>(t + align256(sizeof(uint64_t) * n));
+  uint32_t* hist = reinterpret_cast<uint32_t*>(t + align256(sizeof(uint64_t) * n) + align256(sizeof(uint32_t) * n));
+  const int nb = std::min(SORT_MAX_BLOCKS, 4 * sm_count());
+  if (cudaMemsetAsync(hist + 256 * (size_t)nb, 0, 256 * sizeof(uint32_t), st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  int fb = 0;
+  if (launch_sort(keys, vals, k1, v1, nullptr, n, key_bits, hist, nb, &fb, st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  if (fb) {
+    if (cudaMemcpyAsync(keys, k1, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return SPLAT2D_ERR_CUDA;
+    if (cudaMemcpyAsync(vals, v1, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return SPLAT2D_ERR_CUDA;
+  }
+  return SPLAT2D_OK;
+}
+
+const char* splat2d_strerror(int code) {
+  switch (code) {
+    case SPLAT2D_OK: return "ok";
+    case SPLAT2D_ERR_INVALID_ARG: return "invalid argument";
+    case SPLAT2D_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case SPLAT2D_ERR_CUDA: return "CUDA error";
+    case SPLAT2D_ERR_CAPACITY: return "instance capacity exceeded";
+    case SPLAT2D_ERR_TIMEOUT: return "bounded wait timed out";
+    case SPLAT2D_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

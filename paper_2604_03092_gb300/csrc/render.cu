@@ -1,0 +1,537 @@
+// Per-tile compositing (forward) and its adjoint (backward).
+//
+// Both kernels are persistent: one CTA per tile-shaped block of pixels pulls
+// (view, tile) work items from an atomic queue ordered longest list first,
+// so many views of uneven size run in one launch.  A tile's sorted surfel
+// list is staged through shared memory in chunks; while staging, each entry's
+// pixel rect is tested against every warp's 8x4 pixel patch and the result is
+// kept as one bit per (warp, entry), so a warp only visits entries that can
+// reach its pixels.
+//
+// Forward (Eq. 1): front to back, alpha = min(alpha_max, sigma * G), pairs
+// below alpha_min skipped, stop before T would fall below t_min; the warp
+// leaves the chunk as soon as all its pixels have stopped.
+// Backward: back to front from each pixel's last blended entry, T recovered
+// by division, one scalar suffix sum per pixel (the upstream gradient dotted
+// with the features of the entries behind), per-entry gradients summed across
+// the warp by a transposing butterfly (16 values in 16 shuffles), across the
+// CTA in shared memory, then one set of vector atomics per (tile, entry).
+#include <cuda_runtime.h>
+
+#include "splat2d_internal.cuh"
+
+namespace s2d {
+
+// Shared-memory copy of a render record (unpacked), 96 bytes.
+struct SRec {
+  float4 c;   // cx_hi, cy_hi, cx_lo, cy_lo
+  float4 p;   // p00 p01 p10 p11
+  float4 q;   // p20 p21 p22 opacity
+  float4 col; // r g b z
+  float4 n;   // nx ny nz -
+  int4 rect;  // x0 y0 (x1 - x0) (y1 - y0)
+};
+
+__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRec& o) {
+  const float4 f0 = __ldg(rec + 0), f1 = __ldg(rec + 1), f2 = __ldg(rec + 2), f3 = __ldg(rec + 3),
+               f4 = __ldg(rec + 4);
+  const float2 lo = unpack_half2_scaled(__float_as_uint(f0.z));
+  o.c = make_float4(f0.x, f0.y, lo.x, lo.y);
+  o.p = f1;
+  o.q = make_float4(f2.x, f2.y, f2.z, f0.w);
+  o.col = make_float4(f2.w, f3.x, f3.y, f4.y);
+  o.n = make_float4(f3.z, f3.w, f4.x, 0.f);
+  const uint32_t r0 = __float_as_uint(f4.z), r1 = __float_as_uint(f4.w);
+  const int x0 = (int)(r0 & 0xffffu), y0 = (int)(r0 >> 16), x1 = (int)(r1 & 0xffffu), y1 = (int)(r1 >> 16);
+  o.rect = make_int4(x0, y0, x1 - x0, y1 - y0);
+}
+
+// alpha of one (pixel, record) pair.  Written with explicit round-to-nearest
+// intrinsics so the forward and the backward compute identical bits.
+struct Pair {
+  float alpha, G, a, b, rc, rho, dx, dy;
+  bool obj, clamped;
+};
+__device__ __forceinline__ void eval_pair(const float4 c, const float4 p, const float4 q, float px, float py,
+                                          float lp_scale, float alpha_max, Pair& e) {
+  e.dx = __fsub_rn(__fsub_rn(px, c.x), c.z);
+  e.dy = __fsub_rn(__fsub_rn(py, c.y), c.w);
+  e.a = __fmaf_rn(p.x, e.dx, __fmul_rn(p.y, e.dy));
+  e.b = __fmaf_rn(p.z, e.dx, __fmul_rn(p.w, e.dy));
+  const float cc = __fmaf_rn(q.x, e.dx, __fmaf_rn(q.y, e.dy, q.z));
+  e.rc = rcp_approx(cc);
+  const float ua = __fmul_rn(e.a, e.rc), vb = __fmul_rn(e.b, e.rc);
+  const float ro = __fmaf_rn(ua, ua, __fmul_rn(vb, vb));
+  const float rl = __fmul_rn(lp_scale, __fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)));
+  e.obj = ro <= rl;  // false for NaN (c = 0): the low-pass term decides
+  e.rho = e.obj ? ro : rl;
+  e.G = ex2_approx(-e.rho);
+  const float raw = __fmul_rn(q.w, e.G);
+  e.clamped = raw > alpha_max;
+  e.alpha = e.clamped ? alpha_max : raw;
+}
+
+__device__ __forceinline__ bool in_rect(const int4 r, int px, int py) {
+  return (unsigned)(px - r.x) <= (unsigned)r.z && (unsigned)(py - r.y) <= (unsigned)r.w;
+}
+
+struct RenderArgs {
+  const DView* views;
+  int32_t V;
+  int64_t T;
+  const uint2* ranges;
+  const uint32_t* order;
+  const uint32_t* vals;
+  const float4* records;
+  float* rgrad;
+  RastParams P;
+  Header* hdr;
+  float* rgb;
+  float* depth;
+  float* normal;
+  float* alpha;
+  float* tfinal;
+  uint32_t* last;
+  const float* d_rgb;
+  const float* d_depth;
+  const float* d_normal;
+  const float* d_alpha;
+};
+
+// Stage entries [base, base + count) of the sorted list into shared memory
+// and build the per-warp visit masks.
+template <int TW, int TH, int CHUNK>
+__device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int64_t base, int count,
+                                            int tx0, int ty0, SRec* s_rec, uint32_t* s_mask, uint32_t* s_idx) {
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int jb = wid * 32; jb < CHUNK; jb += NT) {
+    const int j = jb + lane;
+    uint32_t m = 0;
+    if (j < count) {
+      const uint32_t s = __ldg(A.vals + base + j);
+      const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
+      SRec r;
+      unpack_record(A.records + rec * REC_F4, r);
+      s_rec[j] = r;
+      if (s_idx) s_idx[j] = (uint32_t)rec;
+#pragma unroll
+      for (int w = 0; w < NW; w++) {
+        const int bx = tx0 + (w % WX) * 8, by = ty0 + (w / WX) * 4;
+        const bool hit = r.rect.x <= bx + 7 && r.rect.x + r.rect.z >= bx && r.rect.y <= by + 3 &&
+                         r.rect.y + r.rect.w >= by;
+        m |= (uint32_t)hit << w;
+      }
+    }
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, (m >> w) & 1u);
+      if (lane == 0) s_mask[w * (CHUNK / 32) + (jb >> 5)] = bal;
+    }
+  }
+}
+
+template <int TW, int TH, int CHUNK>
+__global__ void __launch_bounds__(TW* TH) k_render_fwd(const RenderArgs A) {
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+  __shared__ SRec s_rec[CHUNK];
+  __shared__ uint32_t s_mask[NW * (CHUNK / 32)];
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const RastParams& P = A.P;
+  uint32_t n_eval = 0, n_blend = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&A.hdr->queue_fwd, 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= A.T) break;
+    const int t = (int)__ldg(A.order + item);
+    const int v = find_view_by_tile(A.views, A.V, t);
+    const DView& vw = A.views[v];
+    const int lt = t - vw.tile_base;
+    const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
+    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7);
+    const int ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
+    const bool inside = ipx < vw.W && ipy < vw.H;
+    const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
+    const uint2 range = __ldg(A.ranges + t);
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
+    uint32_t last = range.x;
+    bool done = !inside;
+    for (int64_t base = range.x; base < range.y; base += CHUNK) {
+      if (__syncthreads_count(!done) == 0) break;
+      const int count = (int)min64(CHUNK, (int64_t)range.y - base);
+      stage_chunk<TW, TH, CHUNK>(A, vw, base, count, tx0, ty0, s_rec, s_mask, nullptr);
+      __syncthreads();
+      if (!__all_sync(0xffffffffu, done)) {
+        for (int wd = 0; wd < CHUNK / 32; wd++) {
+          uint32_t bits = s_mask[wid * (CHUNK / 32) + wd];
+          while (bits) {
+            const int j = wd * 32 + __ffs(bits) - 1;
+            bits &= bits - 1;
+            if (done) continue;
+            const int4 rc = s_rec[j].rect;
+            if (!in_rect(rc, ipx, ipy)) continue;
+            Pair e;
+            eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
+            n_eval++;
+            if (e.alpha < P.alpha_min) continue;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
+            if (Tn < P.t_min) {
+              done = true;
+              continue;
+            }
+            const float w = __fmul_rn(e.alpha, T);
+            const float4 col = s_rec[j].col, nrm = s_rec[j].n;
+            C0 = __fmaf_rn(w, col.x, C0);
+            C1 = __fmaf_rn(w, col.y, C1);
+            C2 = __fmaf_rn(w, col.z, C2);
+            D = __fmaf_rn(w, col.w, D);
+            N0 = __fmaf_rn(w, nrm.x, N0);
+            N1 = __fmaf_rn(w, nrm.y, N1);
+            N2 = __fmaf_rn(w, nrm.z, N2);
+            T = Tn;
+            last = (uint32_t)(base + j + 1);
+            n_blend++;
+          }
+          if (__all_sync(0xffffffffu, done)) break;
+        }
+      }
+    }
+    if (inside) {
+      const int64_t HW = (int64_t)vw.W * vw.H;
+      const int64_t pix = (int64_t)ipy * vw.W + ipx;
+      if (A.rgb) {
+        float* o = A.rgb + 3 * vw.poff + pix;
+        o[0] = __fmaf_rn(T, P.bg[0], C0);
+        o[HW] = __fmaf_rn(T, P.bg[1], C1);
+        o[2 * HW] = __fmaf_rn(T, P.bg[2], C2);
+      }
+      if (A.depth) A.depth[vw.poff + pix] = D;
+      if (A.normal) {
+        float* o = A.normal + 3 * vw.poff + pix;
+        o[0] = N0;
+        o[HW] = N1;
+        o[2 * HW] = N2;
+      }
+      if (A.alpha) A.alpha[vw.poff + pix] = 1.f - T;
+      A.tfinal[vw.poff + pix] = T;
+      A.last[vw.poff + pix] = last;
+    }
+  }
+  if (P.stats) {
+    unsigned long long a = n_eval, b = n_blend;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.hdr->stat[STAT_FWD_EVAL], a);
+      atomicAdd(&A.hdr->stat[STAT_FWD_BLEND], b);
+    }
+  }
+}
+
+// Sum 16 per-lane values over the warp; afterwards lane L (and L ^ 1) holds
+// the total of value index (L >> 1) & 15 in v[0].
+__device__ __forceinline__ void warp_transpose_sum16(float (&v)[16], int lane) {
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const bool up = lane & 16;
+    const float send = up ? v[i] : v[i + 8];
+    const float keep = up ? v[i + 8] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const bool up = lane & 8;
+    const float send = up ? v[i] : v[i + 4];
+    const float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const bool up = lane & 4;
+    const float send = up ? v[i] : v[i + 2];
+    const float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  {
+    const bool up = lane & 2;
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+constexpr int SGRAD_STRIDE = 17;
+
+template <int TW, int TH, int CHUNK>
+__global__ void __launch_bounds__(TW* TH) k_render_bwd(const RenderArgs A) {
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+  __shared__ SRec s_rec[CHUNK];
+  __shared__ uint32_t s_mask[NW * (CHUNK / 32)];
+  __shared__ uint32_t s_idx[CHUNK];
+  __shared__ float s_grad[CHUNK * SGRAD_STRIDE];
+  __shared__ int s_item;
+  __shared__ uint32_t s_top;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const RastParams& P = A.P;
+  uint32_t n_eval = 0, n_blend = 0;
+  for (int i = threadIdx.x; i < CHUNK * SGRAD_STRIDE; i += NT) s_grad[i] = 0.f;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&A.hdr->queue_bwd, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= A.T) break;
+    const int t = (int)__ldg(A.order + item);
+    const int v = find_view_by_tile(A.views, A.V, t);
+    const DView& vw = A.views[v];
+    const int lt = t - vw.tile_base;
+    const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
+    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7);
+    const int ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
+    const bool inside = ipx < vw.W && ipy < vw.H;
+    const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
+    const uint2 range = __ldg(A.ranges + t);
+    // per-pixel state
+    const int64_t HW = (int64_t)vw.W * vw.H;
+    const int64_t pix = (int64_t)ipy * vw.W + ipx;
+    uint32_t my_last = range.x;
+    float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dA = 0.f;
+    if (inside) {
+      my_last = A.last[vw.poff + pix];
+      T = A.tfinal[vw.poff + pix];
+      if (A.d_rgb) {
+        const float* g = A.d_rgb + 3 * vw.poff + pix;
+        dC0 = g[0]; dC1 = g[HW]; dC2 = g[2 * HW];
+      }
+      if (A.d_depth) dD = A.d_depth[vw.poff + pix];
+      if (A.d_normal) {
+        const float* g = A.d_normal + 3 * vw.poff + pix;
+        dN0 = g[0]; dN1 = g[HW]; dN2 = g[2 * HW];
+      }
+      if (A.d_alpha) dA = A.d_alpha[vw.poff + pix];
+    }
+    const float T_final = T;
+    float Q = T_final * (dC0 * P.bg[0] + dC1 * P.bg[1] + dC2 * P.bg[2]);
+    const float dAT = dA * T_final;
+    if (threadIdx.x == 0) s_top = range.x;
+    __syncthreads();
+    if (my_last > range.x) atomicMax(&s_top, my_last);
+    __syncthreads();
+    const uint32_t top = s_top;
+    for (int64_t hi = top; hi > (int64_t)range.x; hi -= CHUNK) {
+      const int64_t lo = max64((int64_t)range.x, hi - CHUNK);
+      const int count = (int)(hi - lo);
+      stage_chunk<TW, TH, CHUNK>(A, vw, lo, count, tx0, ty0, s_rec, s_mask, s_idx);
+      __syncthreads();
+      for (int wd = CHUNK / 32 - 1; wd >= 0; wd--) {
+        uint32_t bits = s_mask[wid * (CHUNK / 32) + wd];
+        while (bits) {
+          const int jj = 31 - __clz(bits);
+          bits &= ~(1u << jj);
+          const int j = wd * 32 + jj;
+          const uint32_t i = (uint32_t)(lo + j);
+          bool act = false;
+          Pair e;
+          const int4 rc = s_rec[j].rect;
+          if (i < my_last && in_rect(rc, ipx, ipy)) {
+            eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
+            n_eval++;
+            act = e.alpha >= P.alpha_min;
+          }
+          if (!__any_sync(0xffffffffu, act)) continue;
+          float g[16];
+          float gz = 0.f;
+#pragma unroll
+          for (int k = 0; k < 16; k++) g[k] = 0.f;
+          if (act) {
+            n_blend++;
+            const float4 col = s_rec[j].col, nrm = s_rec[j].n, pp = s_rec[j].p, qq = s_rec[j].q;
+            const float iom = rcp_approx(__fsub_rn(1.f, e.alpha));
+            const float Ti = T * iom;
+            const float w = e.alpha * Ti;
+            const float f = fmaf(dC0, col.x, fmaf(dC1, col.y, fmaf(dC2, col.z, fmaf(dD, col.w,
+                            fmaf(dN0, nrm.x, fmaf(dN1, nrm.y, dN2 * nrm.z))))));
+            const float da = Ti * f - (Q - dAT) * iom;
+            Q = fmaf(w, f, Q);
+            T = Ti;
+            g[G_R] = w * dC0;
+            g[G_G] = w * dC1;
+            g[G_B] = w * dC2;
+            gz = w * dD;
+            g[G_NX] = w * dN0;
+            g[G_NY] = w * dN1;
+            g[G_NZ] = w * dN2;
+            if (!e.clamped) {
+              g[G_OP] = da * e.G;
+              const float drho = -kLn2 * e.G * (da * qq.w);
+              float ddx, ddy;
+              if (e.obj) {
+                const float t2 = 2.f * drho * e.rc * e.rc;
+                const float gA = t2 * e.a, gB = t2 * e.b, gC = -2.f * drho * e.rho * e.rc;
+                g[G_P00] = gA * e.dx;
+                g[G_P01] = gA * e.dy;
+                g[G_P10] = gB * e.dx;
+                g[G_P11] = gB * e.dy;
+                g[G_P20] = gC * e.dx;
+                g[G_P21] = gC * e.dy;
+                g[G_P22] = gC;
+                ddx = gA * pp.x + gB * pp.z + gC * qq.x;
+                ddy = gA * pp.y + gB * pp.w + gC * qq.y;
+              } else {
+                ddx = 2.f * P.lp_scale * e.dx * drho;
+                ddy = 2.f * P.lp_scale * e.dy * drho;
+              }
+              g[G_CX] = -ddx;
+              g[G_CY] = -ddy;
+            }
+          }
+          warp_transpose_sum16(g, lane);
+          for (int o = 16; o > 0; o >>= 1) gz += __shfl_xor_sync(0xffffffffu, gz, o);
+          if ((lane & 1) == 0) atomicAdd(&s_grad[j * SGRAD_STRIDE + (lane >> 1)], g[0]);
+          if (lane == 1) atomicAdd(&s_grad[j * SGRAD_STRIDE + 16], gz);
+        }
+      }
+      __syncthreads();
+      // flush this chunk's per-entry sums: one set of vector atomics per entry
+      for (int j = threadIdx.x; j < count; j += NT) {
+        float* sg = s_grad + j * SGRAD_STRIDE;
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 17; k++) acc += fabsf(sg[k]);
+        if (acc != 0.f) {
+          float* dst = A.rgrad + (int64_t)s_idx[j] * GRAD_F;
+          red_add_v4(dst + 0, sg[0], sg[1], sg[2], sg[3]);
+          red_add_v4(dst + 4, sg[4], sg[5], sg[6], sg[7]);
+          red_add_v4(dst + 8, sg[8], sg[9], sg[10], sg[11]);
+          red_add_v4(dst + 12, sg[12], sg[13], sg[14], sg[15]);
+          atomicAdd(dst + 16, sg[16]);
+#pragma unroll
+          for (int k = 0; k < 17; k++) sg[k] = 0.f;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (P.stats) {
+    unsigned long long a = n_eval, b = n_blend;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      atomicAdd(&A.hdr->stat[STAT_BWD_EVAL], a);
+      atomicAdd(&A.hdr->stat[STAT_BWD_BLEND], b);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch
+// ---------------------------------------------------------------------------
+static RenderArgs make_args(const Layout& L, const RastParams& P, char* ws, const uint32_t* vals) {
+  RenderArgs A;
+  A.views = reinterpret_cast<const DView*>(ws + L.views);
+  A.V = L.V;
+  A.T = L.T;
+  A.ranges = reinterpret_cast<const uint2*>(ws + L.ranges);
+  A.order = reinterpret_cast<const uint32_t*>(ws + L.tile_order);
+  A.vals = vals;
+  A.records = reinterpret_cast<const float4*>(ws + L.records);
+  A.rgrad = reinterpret_cast<float*>(ws + L.rgrad);
+  A.P = P;
+  A.hdr = reinterpret_cast<Header*>(ws + L.header);
+  A.tfinal = reinterpret_cast<float*>(ws + L.tfinal);
+  A.last = reinterpret_cast<uint32_t*>(ws + L.last);
+  A.rgb = A.depth = A.normal = A.alpha = nullptr;
+  A.d_rgb = A.d_depth = A.d_normal = A.d_alpha = nullptr;
+  return A;
+}
+
+template <typename K>
+static int persistent_grid(K kernel, int threads, int64_t work) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t g = (int64_t)per_sm * sm_count();
+  if (g > work) g = work;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int TW, int TH, int CHUNK>
+static cudaError_t run_fwd(const RenderArgs& A, cudaStream_t st) {
+  auto k = k_render_fwd<TW, TH, CHUNK>;
+  static int grid = -1;
+  static int64_t grid_T = -1;
+  if (grid < 0 || grid_T != A.T) {
+    grid = persistent_grid(k, TW * TH, A.T);
+    grid_T = A.T;
+  }
+  k<<<grid, TW * TH, 0, st>>>(A);
+  return cudaGetLastError();
+}
+template <int TW, int TH, int CHUNK>
+static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
+  auto k = k_render_bwd<TW, TH, CHUNK>;
+  static int grid = -1;
+  static int64_t grid_T = -1;
+  if (grid < 0 || grid_T != A.T) {
+    grid = persistent_grid(k, TW * TH, A.T);
+    grid_T = A.T;
+  }
+  k<<<grid, TW * TH, 0, st>>>(A);
+  return cudaGetLastError();
+}
+
+#define S2D_DISPATCH(FN, TWv, THv, CH, ...)                                   \
+  do {                                                                        \
+    if (TWv == 16 && THv == 16) {                                             \
+      if (CH == 64) return FN<16, 16, 64>(__VA_ARGS__);                       \
+      if (CH == 128) return FN<16, 16, 128>(__VA_ARGS__);                     \
+      if (CH == 256) return FN<16, 16, 256>(__VA_ARGS__);                     \
+    } else if (TWv == 8 && THv == 8) {                                        \
+      if (CH == 64) return FN<8, 8, 64>(__VA_ARGS__);                         \
+      if (CH == 128) return FN<8, 8, 128>(__VA_ARGS__);                       \
+      if (CH == 256) return FN<8, 8, 256>(__VA_ARGS__);                       \
+    } else if (TWv == 32 && THv == 8) {                                       \
+      if (CH == 64) return FN<32, 8, 64>(__VA_ARGS__);                        \
+      if (CH == 128) return FN<32, 8, 128>(__VA_ARGS__);                      \
+      if (CH == 256) return FN<32, 8, 256>(__VA_ARGS__);                      \
+    }                                                                         \
+    return cudaErrorInvalidValue;                                             \
+  } while (0)
+
+cudaError_t launch_render_fwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
+                              float* rgb, float* depth, float* normal, float* alpha, cudaStream_t st) {
+  if (L.T <= 0) return cudaSuccess;
+  RenderArgs A = make_args(L, P, ws, vals);
+  A.rgb = rgb;
+  A.depth = depth;
+  A.normal = normal;
+  A.alpha = alpha;
+  Header* hdr = reinterpret_cast<Header*>(ws + L.header);
+  cudaError_t e = cudaMemsetAsync(&hdr->queue_fwd, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  S2D_DISPATCH(run_fwd, P.tile_w, P.tile_h, chunk, A, st);
+}
+
+cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
+                              const float* d_rgb, const float* d_depth, const float* d_normal,
+                              const float* d_alpha, cudaStream_t st) {
+  if (L.T <= 0) return cudaSuccess;
+  RenderArgs A = make_args(L, P, ws, vals);
+  A.d_rgb = d_rgb;
+  A.d_depth = d_depth;
+  A.d_normal = d_normal;
+  A.d_alpha = d_alpha;
+  Header* hdr = reinterpret_cast<Header*>(ws + L.header);
+  cudaError_t e = cudaMemsetAsync(&hdr->queue_bwd, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  S2D_DISPATCH(run_bwd, P.tile_w, P.tile_h, chunk, A, st);
+}
+
+}  // namespace s2d

@@ -1,0 +1,301 @@
+"""Python binding of libsplat2d: argument marshalling around the C ABI.
+
+Every step of the rasterizer runs in the CUDA library; this module only
+turns torch tensors into device pointers, owns the workspace tensor and
+wraps the backward in a `torch.autograd.Function`.  There is no fallback:
+if the library cannot be loaded, or a tensor is not on a CUDA device, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+from typing import List, NamedTuple, Optional, Sequence
+
+import torch
+
+from . import _abi
+
+__all__ = ["RasterConfig", "Rasterizer", "Images", "SurfelGrads", "Splat2DRender", "render"]
+
+
+@dataclasses.dataclass
+class RasterConfig:
+    """Constants of the rasterizer (see splat2d_config in include/splat2d.h)."""
+
+    tile_w: int = 16
+    tile_h: int = 16
+    chunk: int = 256
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    lowpass_sigma: float = math.sqrt(0.5)
+    z_near: float = 0.01
+    bg: tuple = (0.0, 0.0, 0.0)
+    stats: bool = True
+
+    def to_c(self) -> _abi.Config:
+        c = _abi.Config()
+        c.tile_w, c.tile_h, c.chunk = int(self.tile_w), int(self.tile_h), int(self.chunk)
+        c.alpha_min, c.alpha_max, c.t_min = self.alpha_min, self.alpha_max, self.t_min
+        c.lowpass_sigma, c.z_near = self.lowpass_sigma, self.z_near
+        for i in range(3):
+            c.bg[i] = float(self.bg[i])
+        c.flags = 0 if self.stats else _abi.FLAG_NO_STATS
+        return c
+
+
+class Images(NamedTuple):
+    rgb: torch.Tensor     # [V, 3, H, W] for equal-size views, else packed [3 * P]
+    depth: torch.Tensor   # [V, H, W] or packed [P]
+    normal: torch.Tensor  # [V, 3, H, W] or packed [3 * P]
+    alpha: torch.Tensor   # [V, H, W] or packed [P]
+
+
+class SurfelGrads(NamedTuple):
+    means: torch.Tensor
+    scales: torch.Tensor
+    quats: torch.Tensor
+    opacity: torch.Tensor
+    rgb: torch.Tensor
+    pose: torch.Tensor  # [V, 6] dL/d(rho, phi) of T_cw <- Exp(xi) T_cw at xi = 0
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libsplat2d takes CUDA tensors only")
+    if t.dtype != torch.float32:
+        raise ValueError(f"expected float32, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Rasterizer:
+    """One rasterization problem: a set of views, a surfel count, the
+    constants, and the workspace that holds every intermediate buffer.
+
+    `views` are `scenes.View`-like objects (width, height, fx, fy, cx, cy,
+    Rt (3x4 world->camera), surfel_offset, surfel_count).  Images of the
+    views are packed one after another.  A forward and its backward must use
+    the same Rasterizer with no other forward in between.
+    """
+
+    def __init__(self, views: Sequence, n_surfels: int, config: Optional[RasterConfig] = None,
+                 capacity: Optional[int] = None, device=None):
+        self.lib = _abi.load()
+        self.config = config or RasterConfig()
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("the rasterizer runs on CUDA devices only")
+        self.n_surfels = int(n_surfels)
+        self.n_views = len(views)
+        if self.n_views < 1:
+            raise ValueError("at least one view is required")
+        self._cviews = (_abi.View * self.n_views)()
+        self.sizes = []
+        pix = 0
+        for i, v in enumerate(views):
+            cv = self._cviews[i]
+            cv.width, cv.height = int(v.width), int(v.height)
+            cv.fx, cv.fy, cv.cx, cv.cy = float(v.fx), float(v.fy), float(v.cx), float(v.cy)
+            Rt = [float(x) for x in (v.Rt.reshape(-1).tolist() if hasattr(v.Rt, "reshape") else v.Rt)]
+            for k in range(12):
+                cv.Rt[k] = Rt[k]
+            cnt = getattr(v, "surfel_count", -1)
+            off = getattr(v, "surfel_offset", 0)
+            cv.surfel_offset = int(off)
+            cv.surfel_count = int(self.n_surfels - off if cnt is None or cnt < 0 else cnt)
+            cv.pixel_offset = pix
+            self.sizes.append((cv.height, cv.width))
+            pix += cv.width * cv.height
+        self.n_pixels = pix
+        self.uniform = len(set(self.sizes)) == 1
+        self.n_records = sum(int(self._cviews[i].surfel_count) for i in range(self.n_views))
+        self._cfg = self.config.to_c()
+        cap = capacity if capacity is not None else max(1 << 16, int(1.5 * self.n_records))
+        self._alloc(cap)
+
+    # -- workspace ---------------------------------------------------------
+    def _problem(self, cap: int) -> _abi.Problem:
+        p = _abi.Problem()
+        p.views = ctypes.cast(self._cviews, ctypes.POINTER(_abi.View))
+        p.n_views = self.n_views
+        p.n_surfels = self.n_surfels
+        p.instance_capacity = int(cap)
+        return p
+
+    def _alloc(self, cap: int):
+        self.capacity = int(min(cap, 0xFFFFFFFF))
+        self._prob = self._problem(self.capacity)
+        size = self.lib.splat2d_workspace_size(ctypes.byref(self._cfg), ctypes.byref(self._prob))
+        if size == 0:
+            raise ValueError("invalid rasterizer problem (check views, surfel ranges and the config)")
+        self.ws_bytes = int(size)
+        self.ws = None
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self._ws_ptr = (base + 255) & ~255
+        lay = _abi.Layout()
+        _abi.check(self.lib.splat2d_workspace_layout(ctypes.byref(self._cfg), ctypes.byref(self._prob),
+                                                     ctypes.byref(lay)), "workspace layout")
+        self.layout = lay
+
+    def ws_tensor(self, offset: int, count: int, dtype: torch.dtype) -> torch.Tensor:
+        """A typed view of `count` elements at byte `offset` of the workspace."""
+        start = self._ws_ptr - self.ws.data_ptr() + int(offset)
+        nbytes = int(count) * torch.empty((), dtype=dtype).element_size()
+        return self.ws[start:start + nbytes].view(dtype)
+
+    def set_capacity(self, cap: int):
+        if int(cap) != self.capacity:
+            self._alloc(int(cap))
+
+    def set_config(self, config: RasterConfig):
+        self.config = config
+        self._cfg = config.to_c()
+        self._alloc(self.capacity)
+
+    # -- buffers -----------------------------------------------------------
+    def new_images(self) -> Images:
+        P = self.n_pixels
+        dev = self.device
+        return Images(torch.empty(3 * P, device=dev), torch.empty(P, device=dev), torch.empty(3 * P, device=dev),
+                      torch.empty(P, device=dev))
+
+    def shaped(self, im: Images) -> Images:
+        """[V,3,H,W] / [V,H,W] views of packed images when all views share a size."""
+        if not self.uniform:
+            return im
+        H, W = self.sizes[0]
+        V = self.n_views
+        return Images(im.rgb.view(V, 3, H, W), im.depth.view(V, H, W), im.normal.view(V, 3, H, W),
+                      im.alpha.view(V, H, W))
+
+    def view_images(self, im: Images, v: int) -> Images:
+        """Images of view v as ([3,H,W], [H,W], [3,H,W], [H,W])."""
+        H, W = self.sizes[v]
+        o = int(self._cviews[v].pixel_offset)
+        flat = [t.reshape(-1) for t in im]
+        return Images(flat[0][3 * o:3 * o + 3 * H * W].view(3, H, W), flat[1][o:o + H * W].view(H, W),
+                      flat[2][3 * o:3 * o + 3 * H * W].view(3, H, W), flat[3][o:o + H * W].view(H, W))
+
+    @staticmethod
+    def _surfels(means, scales, quats, opacity, rgb) -> _abi.Surfels:
+        s = _abi.Surfels()
+        s.means, s.scales, s.quats = _ptr(means), _ptr(scales), _ptr(quats)
+        s.opacity, s.rgb = _ptr(opacity), _ptr(rgb)
+        s.n = means.shape[0]
+        return s
+
+    # -- calls -------------------------------------------------------------
+    def preprocess(self, means, scales, quats, opacity, rgb):
+        if means.shape[0] != self.n_surfels:
+            raise ValueError(f"expected {self.n_surfels} surfels, got {means.shape[0]}")
+        self._sf = self._surfels(means, scales, quats, opacity, rgb)
+        _abi.check(self.lib.splat2d_preprocess(ctypes.byref(self._cfg), ctypes.byref(self._prob),
+                                               ctypes.byref(self._sf), self._ws_ptr, self.ws_bytes, _stream()),
+                   "splat2d_preprocess")
+
+    def bin_sort(self):
+        _abi.check(self.lib.splat2d_bin_sort(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
+                                             self.ws_bytes, _stream()), "splat2d_bin_sort")
+
+    def render_fwd(self, out: Images):
+        _abi.check(self.lib.splat2d_render_fwd(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
+                                               self.ws_bytes, _ptr(out.rgb), _ptr(out.depth), _ptr(out.normal),
+                                               _ptr(out.alpha), _stream()), "splat2d_render_fwd")
+
+    def render_bwd(self, means, scales, quats, opacity, rgb, d_out: Sequence[Optional[torch.Tensor]],
+                   grads: SurfelGrads):
+        sf = self._surfels(means, scales, quats, opacity, rgb)
+        g = _abi.Grads()
+        g.means, g.scales, g.quats = _ptr(grads.means), _ptr(grads.scales), _ptr(grads.quats)
+        g.opacity, g.rgb, g.pose = _ptr(grads.opacity), _ptr(grads.rgb), _ptr(grads.pose)
+        d = [None if t is None else _ptr(t) for t in d_out]
+        _abi.check(self.lib.splat2d_render_bwd(ctypes.byref(self._cfg), ctypes.byref(self._prob), ctypes.byref(sf),
+                                               self._ws_ptr, self.ws_bytes, d[0], d[1], d[2], d[3], ctypes.byref(g),
+                                               _stream()), "splat2d_render_bwd")
+
+    def stats(self) -> dict:
+        """Synchronises; device status and pair counters of the last iteration."""
+        st = _abi.Stats()
+        self.lib.splat2d_stats(self._ws_ptr, ctypes.byref(st), _stream())
+        return {k: getattr(st, k) for k, _ in _abi.Stats._fields_ if k != "reserved"}
+
+    def status(self) -> int:
+        need = ctypes.c_int64(0)
+        rc = self.lib.splat2d_status(self._ws_ptr, ctypes.byref(need), _stream())
+        self._needed = int(need.value)
+        return int(rc)
+
+    def forward(self, means, scales, quats, opacity, rgb, out: Optional[Images] = None, check: bool = True,
+                max_retries: int = 3) -> Images:
+        """preprocess -> bin_sort -> render_fwd.  With check=True the device
+        status is read (a synchronisation) and an instance-capacity overflow
+        is repaired by growing the workspace and running again."""
+        out = out or self.new_images()
+        for _ in range(max_retries + 1):
+            self.preprocess(means, scales, quats, opacity, rgb)
+            self.bin_sort()
+            self.render_fwd(out)
+            if not check:
+                return out
+            rc = self.status()
+            if rc == _abi.OK:
+                return out
+            if rc != _abi.ERR_CAPACITY:
+                raise _abi.Splat2DError(rc, "device status")
+            self.set_capacity(int(self._needed * 1.25) + 1024)
+        raise _abi.Splat2DError(_abi.ERR_CAPACITY, "instance capacity")
+
+    def new_grads(self) -> SurfelGrads:
+        n, dev = self.n_surfels, self.device
+        z = lambda *s: torch.zeros(*s, device=dev)
+        return SurfelGrads(z(n, 3), z(n, 2), z(n, 4), z(n), z(n, 3), z(self.n_views, 6))
+
+    def backward(self, means, scales, quats, opacity, rgb, d_out: Sequence[Optional[torch.Tensor]],
+                 grads: Optional[SurfelGrads] = None) -> SurfelGrads:
+        """Gradients of sum(d_out . outputs); accumulated into `grads`
+        (zeros if not given).  d_out = (d_rgb, d_depth, d_normal, d_alpha),
+        packed like the forward outputs; None entries count as zero."""
+        grads = grads or self.new_grads()
+        flat = [None if t is None else t.contiguous().view(-1) for t in d_out]
+        self.render_bwd(means, scales, quats, opacity, rgb, flat, grads)
+        return grads
+
+
+class Splat2DRender(torch.autograd.Function):
+    """Differentiable render of all views of `rast`: returns (rgb, depth,
+    normal, alpha).  `pose_tangent` ([V, 6]) receives dL/dxi of each view's
+    pose under T_cw <- Exp(xi) T_cw at xi = 0; its value is not used."""
+
+    @staticmethod
+    def forward(ctx, rast: Rasterizer, means, scales, quats, opacity, rgb, pose_tangent, check: bool = True):
+        params = [t.contiguous() for t in (means, scales, quats, opacity, rgb)]
+        out = rast.forward(*params, check=check)
+        ctx.rast = rast
+        ctx.save_for_backward(*params)
+        shaped = rast.shaped(out)
+        return tuple(shaped)
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_normal, g_alpha):
+        rast: Rasterizer = ctx.rast
+        params = ctx.saved_tensors
+        grads = rast.backward(*params, (g_rgb, g_depth, g_normal, g_alpha))
+        return (None, grads.means, grads.scales, grads.quats, grads.opacity, grads.rgb, grads.pose, None)
+
+
+def render(rast: Rasterizer, means, scales, quats, opacity, rgb, pose_tangent=None, check: bool = True):
+    """Functional form of Splat2DRender."""
+    if pose_tangent is None:
+        pose_tangent = torch.zeros(rast.n_views, 6, device=means.device, requires_grad=False)
+    return Splat2DRender.apply(rast, means, scales, quats, opacity, rgb, pose_tangent, check)

@@ -1,0 +1,364 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle on
+the same seeded inputs.  Bars: sort keys / index lists bit-exact; rendered
+RGB, depth, normal and alpha within 1e-5 absolute on every pixel whose
+discrete decisions the oracle does not report as within rounding (those are
+counted and bounded); gradients within 1e-3 relative L2."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2604_03092_gb300 import _abi, scenes
+from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer, render
+
+from gpu_utils import FWD_ATOL, GRAD_REL_L2, gpu_forward, oracle_cfg, rel_l2, to_dev, upstream, view_stack
+
+pytestmark = pytest.mark.gpu
+
+MAX_FLAGGED = 2e-3  # fraction of pixels whose decisions are within rounding
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _abi.load()
+
+
+# --------------------------------------------------------------------------
+# the radix sort on its own: synthetic keys, bit-exact vs a stable sort
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,key_bits,distinct", [
+    (1, 8, 4), (2, 8, 1), (31, 13, 5), (2047, 32, 100), (2048, 40, 7), (2049, 47, 3000),
+    (100_003, 47, 50), (1_000_000, 64, 1 << 62), (3_000_001, 40, 1 << 20), (524_288, 32, 1)])
+def test_sort_pairs_stable_bit_exact(n, key_bits, distinct):
+    rng = np.random.default_rng(n + key_bits)
+    hi = min(distinct, (1 << key_bits) - 1 if key_bits < 64 else (1 << 63))
+    keys = rng.integers(0, max(hi, 1), size=n, dtype=np.uint64)
+    if key_bits < 64:
+        keys &= np.uint64((1 << key_bits) - 1)
+    vals = np.arange(n, dtype=np.uint32)
+    order = np.argsort(keys, kind="stable")
+    lib = _abi.load()
+    k = torch.from_numpy(keys.view(np.int64)).cuda()
+    v = torch.from_numpy(vals.view(np.int32)).cuda()
+    tmp = torch.empty(lib.splat2d_sort_tmp_size(n) + 256, dtype=torch.uint8, device="cuda")
+    tp = (tmp.data_ptr() + 255) & ~255
+    rc = lib.splat2d_sort_pairs(k.data_ptr(), v.data_ptr(), n, key_bits, tp, tmp.numel() - 256,
+                                torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(k.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(v.cpu().numpy().view(np.uint32), vals[order])
+
+
+# --------------------------------------------------------------------------
+# preprocess and binning
+# --------------------------------------------------------------------------
+
+def _records(rast):
+    lay = rast.layout
+    R = lay.n_records
+    rec = rast.ws_tensor(lay.records, R * 20, torch.float32).view(R, 20).cpu().numpy()
+    nt = rast.ws_tensor(lay.ntiles, R, torch.int32).cpu().numpy().view(np.uint32)
+    return rec, nt
+
+
+def _half_lo(bits):
+    h = np.frombuffer(np.asarray(bits, np.float32).tobytes(), dtype=np.float16).astype(np.float64)
+    return h.reshape(-1, 2) / 65536.0
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_preprocess_matches_oracle(seed):
+    sc = scenes.random_scene(n=4096, seed=seed)
+    cfg = RasterConfig()
+    rast, params, _ = gpu_forward(sc, cfg)
+    rec, nt = _records(rast)
+    p = oracle.preprocess_scene_view(sc, 0, oracle_cfg(cfg))
+    amb = (p.sflags & (oracle.SF_TILE_AMBIG | oracle.SF_NEAR_AMBIG)) != 0
+    vis_o = p.status == oracle.ST_VISIBLE
+    vis_g = nt > 0
+    assert np.array_equal(vis_o[~amb], vis_g[~amb])
+    both = vis_o & vis_g
+    # FP32 depth key: bit-exact
+    zb = rec[:, 17].view(np.uint32)
+    assert np.array_equal(zb[both], p.zbits[both])
+    # pixel rects: exact unless an edge is within rounding of a pixel center
+    r0 = rec[:, 18].view(np.uint32)
+    r1 = rec[:, 19].view(np.uint32)
+    grect = np.stack([r0 & 0xFFFF, r0 >> 16, r1 & 0xFFFF, r1 >> 16], 1).astype(np.int32)
+    pix_ok = both & ((p.sflags & oracle.SF_PIX_AMBIG) == 0)
+    assert np.array_equal(grect[pix_ok], p.pixrect[pix_ok])
+    # projected center (float-float) to ~1e-6 px, colours and opacity exact
+    lo = _half_lo(rec[:, 2])
+    cx = rec[:, 0].astype(np.float64) + lo[:, 0]
+    cy = rec[:, 1].astype(np.float64) + lo[:, 1]
+    assert np.abs(cx[both] - p.rec[both, 9]).max() < 1e-6
+    assert np.abs(cy[both] - p.rec[both, 10]).max() < 1e-6
+    np.testing.assert_array_equal(rec[both, 3], sc.opacity[both])
+    np.testing.assert_array_equal(rec[both][:, [11, 12, 13]], sc.rgb[both])
+    nrm = rec[:, [14, 15, 16]]
+    assert np.abs(nrm[both] - p.rec[both, 12:15]).max() < 1e-6
+    # tile counts follow from the pixel rect
+    tx = grect[:, 2] // 16 - grect[:, 0] // 16 + 1
+    ty = grect[:, 3] // 16 - grect[:, 1] // 16 + 1
+    assert np.array_equal(nt[vis_g], (tx * ty)[vis_g])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_bin_sort_matches_oracle_bit_exact(tile):
+    sc = scenes.random_scene(n=3000, width=100, height=70, f=70.0, seed=4, n_views=3)
+    cfg = RasterConfig(tile_w=tile[0], tile_h=tile[1])
+    rast, params, _ = gpu_forward(sc, cfg)
+    st = rast.stats()
+    n = st["n_instances"]
+    lay = rast.layout
+    keys = rast.ws_tensor(lay.keys, n, torch.int64).cpu().numpy().view(np.uint64)
+    vals = rast.ws_tensor(lay.vals, n, torch.int32).cpu().numpy().view(np.uint32)
+    ocfg = oracle_cfg(cfg)
+    preps = [oracle.preprocess_scene_view(sc, v, ocfg) for v in range(3)]
+    tx = (100 + tile[0] - 1) // tile[0]
+    ty = (70 + tile[1] - 1) // tile[1]
+    okeys, ovals = oracle.bin_sort(preps, [0, tx * ty, 2 * tx * ty], [tx] * 3, [0, 0, 0])
+    # drop (view, surfel) pairs whose tile rect is decided within rounding
+    bad = set()
+    for v, p in enumerate(preps):
+        for s in np.nonzero(p.sflags & (oracle.SF_TILE_AMBIG | oracle.SF_NEAR_AMBIG))[0]:
+            bad.add((v, int(s)))
+
+    def keep(k, vv):
+        view = (k >> np.uint64(32)).astype(np.int64) // (tx * ty)
+        m = np.array([(int(a), int(b)) not in bad for a, b in zip(view, vv)], bool)
+        return k[m], vv[m]
+
+    gk, gv = keep(keys, vals)
+    ok_, ov = keep(okeys, ovals)
+    assert len(gk) == len(ok_)
+    assert np.array_equal(gk, ok_) and np.array_equal(gv, ov)
+    assert len(bad) <= 0.01 * sc.n * 3
+
+
+# --------------------------------------------------------------------------
+# forward images
+# --------------------------------------------------------------------------
+
+def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1):
+    rast, params, im = gpu_forward(sc, cfg)
+    ocfg = oracle_cfg(cfg)
+    flagged = 0
+    total = 0
+    worst = 0.0
+    for v in (range(len(sc.views)) if views is None else views):
+        p = oracle.preprocess_scene_view(sc, v, ocfg)
+        ref = oracle.render(p, mode)
+        gpu = view_stack(rast, im, v)
+        ok = (ref.pflags & oracle.PF_FORWARD) == 0
+        err = np.abs(gpu - ref.out)
+        worst = max(worst, float(err[:, ok].max()))
+        assert err[:, ok].max() <= FWD_ATOL, (v, np.unravel_index(np.argmax(np.where(ok, err.max(0), 0)), ok.shape),
+                                               err[:, ok].max(axis=1))
+        flagged += int((~ok).sum())
+        total += ok.size
+    assert flagged <= max_flagged * total, (flagged, total)
+    return rast, params, im, worst
+
+
+@pytest.mark.parametrize("tile,chunk", [((16, 16), 256), ((16, 16), 64), ((8, 8), 128), ((32, 8), 256)])
+def test_forward_random_scene(tile, chunk):
+    sc = scenes.random_scene(n=4096, seed=0)
+    _check_forward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], chunk=chunk))
+
+
+def test_forward_with_background_and_definition_mode():
+    sc = scenes.random_scene(n=2048, width=72, height=56, f=60.0, seed=9, n_views=2)
+    _check_forward(sc, RasterConfig(bg=(0.2, 0.5, 0.9)), mode=0)
+
+
+def test_forward_keyframe_views_full_size():
+    """The per-pixel keyframe workload at full size: 512x384 surfels rendered
+    from 8 perturbed poses at 512x384."""
+    sc = scenes.keyframe_scene(seed=1001)
+    _check_forward(sc, RasterConfig())
+
+
+def test_forward_deterministic_and_batched_equals_single():
+    sc = scenes.random_scene(n=3000, width=80, height=64, f=60.0, seed=2, n_views=3)
+    cfg = RasterConfig()
+    rast, params, im = gpu_forward(sc, cfg)
+    im2 = rast.forward(*params)
+    for a, b in zip(im, im2):
+        assert torch.equal(a, b)
+    for v in range(3):
+        one = Rasterizer([sc.views[v]], sc.n, cfg)
+        imv = one.forward(*params)
+        a = rast.view_images(im, v)
+        b = one.view_images(imv, 0)
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+
+
+def test_edge_cases():
+    cfg = RasterConfig()
+    # empty surfel range in one view, ragged image sizes, a 1x1 view
+    sc = scenes.random_scene(n=500, width=37, height=29, f=30.0, seed=3, n_views=1)
+    views = [sc.views[0],
+             scenes.View(1, 1, 30.0, 30.0, 0.5, 0.5, sc.views[0].Rt, 0, 500),
+             scenes.View(37, 29, 30.0, 30.0, 18.5, 14.5, sc.views[0].Rt, 100, 0),
+             scenes.View(20, 50, 25.0, 25.0, 10.0, 25.0, sc.views[0].Rt, 250, 250)]
+    sc.views = views
+    rast, params, im = gpu_forward(sc, cfg)
+    ocfg = oracle_cfg(cfg)
+    for v in range(4):
+        p = oracle.preprocess_scene_view(sc, v, ocfg)
+        ref = oracle.render(p)
+        gpu = view_stack(rast, im, v)
+        ok = (ref.pflags & oracle.PF_FORWARD) == 0
+        if ok.any():
+            assert np.abs(gpu - ref.out)[:, ok].max() <= FWD_ATOL
+    assert float(rast.view_images(im, 2).alpha.abs().max()) == 0.0
+    # everything behind the camera: nothing binned, background everywhere
+    sc2 = scenes.random_scene(n=200, seed=5)
+    sc2.means[:, 2] *= -1
+    rast2, _, im2 = gpu_forward(sc2, RasterConfig(bg=(0.1, 0.2, 0.3)))
+    assert rast2.stats()["n_instances"] == 0
+    assert torch.allclose(im2.rgb.view(3, -1)[:, 0], torch.tensor([0.1, 0.2, 0.3], device="cuda"))
+    # a single surfel
+    sc3 = scenes.random_scene(n=1, seed=6)
+    sc3.means[0] = [0.0, 0.0, 2.0]
+    sc3.opacity[0] = 0.9
+    _check_forward(sc3, cfg)
+
+
+def test_capacity_overflow_is_reported_and_repaired():
+    sc = scenes.random_scene(n=2000, seed=1)
+    cfg = RasterConfig()
+    params = to_dev(sc)
+    rast = Rasterizer(sc.views, sc.n, cfg, capacity=100)
+    rast.preprocess(*params)
+    rast.bin_sort()
+    rast.render_fwd(rast.new_images())
+    assert rast.status() == _abi.ERR_CAPACITY
+    need = rast._needed
+    assert need > 100
+    im = rast.forward(*params)  # grows the workspace and re-runs
+    assert rast.capacity >= need and rast.status() == 0
+    ref = Rasterizer(sc.views, sc.n, cfg, capacity=4 * need).forward(*params)
+    for a, b in zip(im, ref):
+        assert torch.equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# gradients
+# --------------------------------------------------------------------------
+
+def _check_backward(sc, cfg, seed=0, tol=GRAD_REL_L2):
+    rast, params, im = gpu_forward(sc, cfg)
+    d_dev, d_views = upstream(rast, seed)
+    grads = rast.backward(*params, d_dev)
+    torch.cuda.synchronize()
+    ocfg = oracle_cfg(cfg)
+    og = None
+    poses = []
+    for v in range(len(sc.views)):
+        p = oracle.preprocess_scene_view(sc, v, ocfg)
+        gv = oracle.render_bwd(sc.means, sc.scales, sc.quats, p, d_views[v])
+        poses.append(gv.pose)
+        if og is None:
+            og = gv
+        else:
+            for name in ("means", "scales", "quats", "opacity", "rgb"):
+                setattr(og, name, getattr(og, name) + getattr(gv, name))
+    out = {}
+    for name in ("means", "scales", "quats", "opacity", "rgb"):
+        out[name] = rel_l2(getattr(grads, name).cpu().numpy(), getattr(og, name))
+    gp = grads.pose.cpu().numpy()
+    out["pose"] = max(rel_l2(gp[v], poses[v]) for v in range(len(sc.views)))
+    for k, e in out.items():
+        assert e <= tol, (k, out)
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_backward_random_scene(seed):
+    sc = scenes.random_scene(n=4096, seed=seed)
+    _check_backward(sc, RasterConfig(bg=(0.3, 0.1, 0.2)), seed=seed)
+
+
+@pytest.mark.parametrize("tile,chunk", [((8, 8), 64), ((32, 8), 128)])
+def test_backward_tile_shapes(tile, chunk):
+    sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=3, n_views=2)
+    _check_backward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], chunk=chunk))
+
+
+def test_backward_keyframe_crop():
+    sc = scenes.keyframe_scene(seed=1001, width=160, height=120, f=125.0, n_views=3)
+    _check_backward(sc, RasterConfig())
+
+
+def test_autograd_function_and_refinement():
+    """The autograd.Function gives the same gradients as the direct calls,
+    and an Adam refinement of a perturbed keyframe lowers an L1 loss."""
+    sc = scenes.keyframe_scene(seed=1002, width=128, height=96, f=100.0, n_views=4)
+    cfg = RasterConfig()
+    params = [p.clone().requires_grad_(True) for p in to_dev(sc)]
+    rast = Rasterizer(sc.views, sc.n, cfg)
+    pose = torch.zeros(len(sc.views), 6, device="cuda", requires_grad=True)
+    rgb, depth, normal, alpha = render(rast, *params, pose_tangent=pose)
+    w = [torch.randn_like(t) for t in (rgb, depth, normal, alpha)]
+    loss = sum((a * b).sum() for a, b in zip(w, (rgb, depth, normal, alpha)))
+    loss.backward()
+    direct = rast.backward(*[p.detach() for p in params], [x.contiguous() for x in w])
+    for p, g in zip(params + [pose], direct):
+        assert rel_l2(p.grad.cpu().numpy(), g.cpu().numpy()) < 1e-5
+    # refinement: start from noisy colours/opacity and fit the ray-cast target
+    tgt_rgb = torch.from_numpy(sc.target_rgb).cuda()
+    tgt_depth = torch.from_numpy(sc.target_depth).cuda()
+    noisy = [p.detach().clone() for p in params]
+    noisy[4] = (noisy[4] + 0.2 * torch.randn_like(noisy[4])).clamp(0, 1)
+    noisy = [p.requires_grad_(True) for p in noisy]
+    opt = torch.optim.Adam([noisy[4], noisy[3]], lr=0.02)
+    losses = []
+    for it in range(30):
+        opt.zero_grad()
+        rgb, depth, _, _ = render(rast, *noisy, check=(it == 0))
+        loss = (rgb - tgt_rgb).abs().mean() + 0.1 * (depth - tgt_depth).abs().mean()
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            noisy[3].clamp_(0.01, 0.99)
+        losses.append(float(loss))
+    assert losses[-1] < 0.8 * losses[0], losses
+
+
+def test_cuda_graph_replay_matches_eager():
+    sc = scenes.random_scene(n=4096, seed=8, n_views=2)
+    cfg = RasterConfig()
+    params = to_dev(sc)
+    rast = Rasterizer(sc.views, sc.n, cfg)
+    eager = rast.forward(*params)  # sizes the capacity
+    d_dev, _ = upstream(rast, 1)
+    g_eager = rast.backward(*params, d_dev)
+    out = rast.new_images()
+    grads = rast.new_grads()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        rast.forward(*params, out=out, check=False)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for t in grads:
+            t.zero_()
+        rast.forward(*params, out=out, check=False)
+        rast.backward(*params, d_dev, grads=grads)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(out, eager):
+        assert torch.equal(a, b)
+    for a, b in zip(grads, g_eager):
+        assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-5
