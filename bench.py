@@ -1,0 +1,492 @@
+#!/usr/bin/env python
+"""Benchmark of the 2DGS rasterizer forward + backward (the refinement step
+of Flash-Mono's mapping backend) on synthetic indoor submaps.
+
+Default workload: one submap of 32 keyframes x 512x384 per-pixel surfels
+(6,291,456 surfels) along a seeded trajectory through a 3-room layout,
+rendered forward and backward from all 32 keyframe poses at 512x384.  One
+step = preprocess + bin/sort + forward compositing + tile adjoint + chain
+rule to surfel parameters and per-view poses, for all 32 views (the upstream
+gradient is the L1 RGB + 0.1 L1 depth loss gradient against the keyframes'
+ray-cast targets, computed once before timing).
+
+Prints one JSON line (see the end of main()).  Under torchrun each rank
+renders its own independent submap (weak scaling, no collective on the
+data path); rank 0 prints the max-over-ranks timing.
+
+--impl reference times the FP64 CPU oracle (the reference statement of the
+method) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "2DGS raster fwd+bwd ms/view & views/s at 6.3M surfels; fraction of roofline"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+# FP32 work per (pixel, surfel) pair of the compositing kernels, counted from
+# the arithmetic of the method (an FMA counts 2):
+#   alpha of a pair: pixel offset from the float-float center 4, the three
+#   ray-splat numerators/denominator 10, rho_obj 5, rho_lowpass 5, select 1,
+#   exponent argument 1, sigma*G 1, clamp and threshold 2            -> 29
+#   blend of a kept pair: T' 2, w 1, 7 accumulations (rgb, depth, normal) 14,
+#   stop test 1                                                       -> 18
+#   reverse of a kept pair: T recovery 2, w 1, upstream dot 13, d alpha 4,
+#   suffix update 2, 7 colour/depth/normal grads 7, opacity 1, d rho 3,
+#   geometry grads 20, center grads 10                                -> 63
+FLOP_EVAL = 29
+FLOP_BLEND = 18
+FLOP_BWD = 63
+
+
+def _workloads():
+    from paper_2604_03092_gb300 import scenes
+    return {
+        "submap32": ("32 keyframes x 512x384 = 6,291,456 surfels, 32 views at 512x384 (fx=fy=400), 3-room layout",
+                     lambda seed: scenes.submap_scene(seed=2001 + seed)),
+        "keyframe8": ("one 512x384 keyframe = 196,608 surfels, 8 perturbed views at 512x384",
+                      lambda seed: scenes.keyframe_scene(seed=1001 + seed)),
+        "random4096": ("4,096 random surfels, one 128x96 view",
+                       lambda seed: scenes.random_scene(n=4096, seed=seed)),
+        "uneven64": ("64 submaps, log-uniform [50k, 2M] surfels, images from {320x240, 512x384, 640x480}, 4 views each",
+                     lambda seed: scenes.uneven_batch_scene(seed=3001 + seed)),
+        "largemap150": ("150 keyframes x 512x384 = 29,491,200 surfels, 6 rooms, 16 views at 640x480 (fx=fy=500)",
+                        lambda seed: scenes.large_map_scene(seed=4001 + seed)),
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd[1:1] = ["-i", self.uuid]
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self) -> dict:
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            d["source"] = "measured"
+            return d
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(sc, n_pix: int, seed: int = 0):
+    """Time the FP64 oracle on one view of the workload: full preprocess of the
+    view's surfel range, forward at n_pix sampled pixels, reverse pass at the
+    same pixels, chain rule; returns (seconds per view extrapolated to every
+    pixel, description)."""
+    import oracle
+    v = 0
+    H, W = sc.views[v].height, sc.views[v].width
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(H * W, size=min(n_pix, H * W), replace=False)).astype(np.int64)
+    cfg = oracle.Config()
+    t0 = time.perf_counter()
+    p = oracle.preprocess_scene_view(sc, v, cfg)
+    t1 = time.perf_counter()
+    oracle.render_pixels(p, pix)
+    t2 = time.perf_counter()
+    g8 = np.zeros((8, H, W))
+    g8.reshape(8, -1)[:, pix] = rng.normal(size=(8, pix.size))
+    off, cnt = sc.view_ranges()[v]
+    sl = slice(off, off + cnt)
+    oracle.render_bwd(sc.means[sl], sc.scales[sl], sc.quats[sl], p, g8, pix=pix)
+    t3 = time.perf_counter()
+    scale = (H * W) / pix.size
+    per_view = (t1 - t0) + (t3 - t1) * scale
+    desc = (f"view 0 of the workload: oracle preprocess of all {cnt} surfels, forward + reverse at "
+            f"{pix.size} random pixels of {H}x{W}, scaled to the full image (measured {t3 - t0:.1f} s)")
+    return per_view, desc, t3 - t0
+
+
+def _omp_threads() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, wl_desc, make):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = make(0)
+    n_pix = args.ref_pixels
+    times = []
+    for i in range(args.warmup + args.steps):
+        per_view, desc, wall = oracle_sample(sc, n_pix, seed=i)
+        if i >= args.warmup:
+            times.append(per_view)
+    per_view = float(np.mean(times))
+    value = 1.0 / per_view
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_view * len(sc.views) * 1e3,
+        "ms_per_view": per_view * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": wl_desc, "views": len(sc.views), "surfels": sc.n},
+        "cpu_baseline": {"value": value, "unit": "views/s", "cores": _omp_threads(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="submap32")
+    ap.add_argument("--tile", default=None, help="WxH, e.g. 16x16 (default: autotune cache or 16x16)")
+    ap.add_argument("--chunk", type=int, default=None)
+    ap.add_argument("--plain-steps", type=int, default=2, help="steps of the per-view plain-launch baseline (0=skip)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-pixels", type=int, default=8192, help="pixels of the oracle CPU-baseline sample")
+    ap.add_argument("--ref-pixels", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--traffic-json", default=None, help="ncu DRAM-byte summary for the roofline kernel")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    wls = _workloads()
+    if args.workload not in wls:
+        raise SystemExit(f"unknown workload {args.workload}; choose from {sorted(wls)}")
+    wl_desc, make = wls[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl_desc, make)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2604_03092_gb300 import autotune
+    from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    sc = make(rank)  # each rank: its own independent submap
+    V = len(sc.views)
+    params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
+              (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
+
+    cfg = RasterConfig(stats=True)
+    tuned = autotune.lookup(sc.views, sc.n) if args.tile is None else None
+    if tuned:
+        cfg.tile_w, cfg.tile_h, cfg.chunk = tuned
+    if args.tile:
+        cfg.tile_w, cfg.tile_h = (int(x) for x in args.tile.lower().split("x"))
+    if args.chunk:
+        cfg.chunk = args.chunk
+    rast = Rasterizer(sc.views, sc.n, cfg, device=dev)
+    im = rast.forward(*params)  # sizes the instance capacity (synchronises once)
+    st0 = rast.stats()
+    rast.set_capacity(int(st0["needed_capacity"] * 1.1) + 4096)
+
+    # upstream gradient of L1 RGB + 0.1 L1 depth against the ray-cast targets
+    if sc.target_rgb is not None and rast.uniform:
+        shaped = rast.shaped(im)
+        trgb = torch.from_numpy(sc.target_rgb).to(dev)
+        tdep = torch.from_numpy(sc.target_depth).to(dev)
+        d_rgb = (torch.sign(shaped.rgb - trgb) / trgb.numel()).contiguous().view(-1)
+        d_depth = (0.1 * torch.sign(shaped.depth - tdep) / tdep.numel()).contiguous().view(-1)
+    else:
+        gen = torch.Generator(device=dev).manual_seed(0)
+        d_rgb = torch.randn(3 * rast.n_pixels, device=dev, generator=gen) * 1e-6
+        d_depth = torch.randn(rast.n_pixels, device=dev, generator=gen) * 1e-7
+    d_out = (d_rgb, d_depth, None, None)
+    out = rast.new_images()
+    grads = rast.new_grads()
+    stages = ["preprocess", "bin_sort", "render_fwd", "render_bwd", "preprocess_bwd"]
+
+    def step(ev=None):
+        for t in grads:
+            t.zero_()
+        if ev is not None:
+            ev[0].record()
+        rast.preprocess(*params)
+        if ev is not None:
+            ev[1].record()
+        rast.bin_sort()
+        if ev is not None:
+            ev[2].record()
+        rast.render_fwd(out)
+        if ev is not None:
+            ev[3].record()
+        rast.render_bwd_tiles(d_out)
+        if ev is not None:
+            ev[4].record()
+        rast.preprocess_bwd(*params, grads)
+        if ev is not None:
+            ev[5].record()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if rast.status() != 0:
+        raise SystemExit(f"device status {rast.status()} after warm-up")
+
+    # ---- timed region: K steps, CUDA events around every stage -------------
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    launches0 = rast.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        t_start.record()
+        for k in range(args.steps):
+            step(evs[k])
+        t_end.record()
+        torch.cuda.synchronize()
+    launches = rast.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
+                for i, s in enumerate(stages)}
+    st = rast.stats()
+    if st["status"] != 0:
+        raise SystemExit(f"device status {st['status']} in the timed region")
+    max_ms = elapsed_ms
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        max_ms = float(t.item())
+    ms_per_step = max_ms / args.steps
+    value = world * V * args.steps / (max_ms / 1e3)
+
+    # ---- the same step replayed from a CUDA graph ----------------------------
+    graph_vps = None
+    try:
+        s = torch.cuda.Stream(device=dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            step()
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(2):
+            g.replay()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.steps):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        graph_vps = V * args.steps / (a.elapsed_time(b) / 1e3)
+        del g
+    except Exception as e:  # report, do not hide
+        graph_vps = f"failed: {e}"
+
+    # ---- per-view plain launches (classic pattern: one view per launch
+    #      sequence, a host sync per view to size the sort) -------------------
+    plain_vps = None
+    if args.plain_steps > 0 and rank == 0:
+        one = Rasterizer([sc.views[0]], sc.n, cfg, device=dev)
+        one_out = one.new_images()
+        one_grads = one.new_grads()
+        H, W = rast.sizes[0]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nviews = 0
+        for _ in range(args.plain_steps):
+            for v in range(V):
+                for i, x in enumerate(sc.views[v].Rt.reshape(-1)):
+                    one._cviews[0].Rt[i] = float(x)
+                one._cviews[0].width, one._cviews[0].height = sc.views[v].width, sc.views[v].height
+                o = int(rast._cviews[v].pixel_offset)
+                dv = (d_rgb[3 * o:3 * o + 3 * H * W], d_depth[o:o + H * W], None, None) \
+                    if rast.uniform else (None, None, None, None)
+                one.forward(*params, out=one_out, check=True)
+                one.render_bwd_tiles(dv)
+                one.preprocess_bwd(*params, one_grads)
+                nviews += 1
+        torch.cuda.synchronize()
+        plain_vps = nviews / (time.perf_counter() - t0)
+        del one
+
+    # ---- end to end through the public API with host buffers -----------------
+    pinned_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                 (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
+    pinned_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in grads]
+    h2d = sum(t.numel() * t.element_size() for t in pinned_in)
+    d2h = sum(t.numel() * t.element_size() for t in pinned_out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.e2e_steps):
+        for dst, src in zip(params, pinned_in):
+            dst.copy_(src, non_blocking=True)
+        step()
+        for dst, src in zip(pinned_out, grads):
+            dst.copy_(src, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b)
+    e2e_vps = V * args.e2e_steps / (e2e_ms / 1e3)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_vps = world * V * args.e2e_steps / (float(t.item()) / 1e3)
+
+    # ---- roofline of the dominant stage ------------------------------------------
+    peaks = _peaks()
+    clocks = clk.summary()
+    lay = rast.layout
+    n_vis = st["n_visible"]
+    n_inst = st["n_instances"]
+    passes = (32 + max(int(lay.n_tiles - 1).bit_length(), 0) + 7) // 8
+    work = {
+        "preprocess": ("hbm", 56 * sum(1 for _ in [0]) * rast.n_surfels + 4 * lay.n_records + 160 * n_vis),
+        "bin_sort": ("hbm", 8 * lay.n_records + 16 * n_vis + 12 * n_inst + passes * 32 * n_inst + 8 * n_inst),
+        "render_fwd": ("alu", FLOP_EVAL * st["fwd_pairs_evaluated"] + FLOP_BLEND * st["fwd_pairs_blended"]),
+        "render_bwd": ("alu", FLOP_EVAL * st["bwd_pairs_evaluated"] + FLOP_BWD * st["bwd_pairs_blended"]),
+        "preprocess_bwd": ("hbm", 4 * lay.n_records + 80 * n_vis + 56 * rast.n_surfels + 52 * rast.n_surfels),
+    }
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    bound, amount = work[dom]
+    sec = stage_ms[dom] / 1e3
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    stage_frac = {}
+    for s in stages:
+        b_, a_ = work[s]
+        t_ = stage_ms[s] / 1e3
+        if b_ == "hbm":
+            stage_frac[s] = {"bound": "hbm", "achieved_gbs": a_ / t_ / 1e9, "frac": a_ / t_ / 1e9 / peaks["hbm_gbs"],
+                             "ms": stage_ms[s]}
+        else:
+            stage_frac[s] = {"bound": "alu", "achieved_tflops": a_ / t_ / 1e12, "frac": a_ / t_ / 1e12 / alu_peak,
+                             "ms": stage_ms[s]}
+    traffic = None
+    if args.traffic_json and os.path.exists(args.traffic_json):
+        try:
+            traffic = json.load(open(args.traffic_json)).get(dom)
+        except Exception:
+            traffic = None
+    if bound == "hbm":
+        achieved = amount / sec / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": f"{peaks['source']} STREAM-style copy"}
+    else:
+        achieved = amount / sec / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (FP32 FMA pipe)"}
+
+    # ---- CPU baseline (the oracle, host cores, bounded sample) -----------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_view, desc, _ = oracle_sample(sc, args.cpu_pixels)
+        cpu = {"value": 1.0 / per_view, "unit": "views/s", "cores": _omp_threads(), "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_view": ms_per_step / V,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded ray-cast indoor submap; stands in for ScanNet/BundleFusion)",
+            "config": {"workload": args.workload, "description": wl_desc, "views": V, "surfels": sc.n,
+                       "tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk, "instances": n_inst,
+                       "visible_pairs": n_vis, "l2": "inputs larger than L2 (records + instances > 129 MB)",
+                       "parallelism": f"{world} independent submap(s), one per GPU"},
+            "stages_ms": stage_ms, "stage_roofline": stage_frac,
+            "roofline": roof, "clocks": clocks,
+            "graph_views_per_s": graph_vps, "plain_per_view_views_per_s": plain_vps,
+            "e2e": {"value": e2e_vps, "unit": "views/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "pairs": {k: st[k] for k in ("fwd_pairs_evaluated", "fwd_pairs_blended", "bwd_pairs_evaluated",
+                                         "bwd_pairs_blended")},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

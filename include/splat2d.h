@@ -30,7 +30,10 @@
  *    the arrays they point to, the workspace and every image buffer.
  *  - The caller owns all memory.  The library never allocates device memory:
  *    the caller allocates a workspace of splat2d_workspace_size() bytes
- *    (256-byte aligned) and passes the same problem to every call.
+ *    (256-byte aligned), zero-fills it once before its first use, and passes
+ *    the same problem to every call.  (The gradient records in the workspace
+ *    are accumulated by the tile adjoint and cleared again by the chain rule,
+ *    so they stay zero between iterations.)
  *  - Calls are asynchronous on `stream`, make no host synchronisation and no
  *    allocation, and are capturable in a CUDA graph (except
  *    splat2d_status / splat2d_stats, which synchronise).
@@ -145,8 +148,8 @@ void splat2d_default_config(splat2d_config* cfg);
 
 /* Bytes of workspace the problem needs (0 if the arguments are invalid).
  * The workspace holds, per (view, surfel) pair of every view's range, an
- * 80-byte render record and a 64-byte gradient record, plus 24 bytes per
- * unit of instance_capacity and 16 bytes per pixel. */
+ * 80-byte render record, an 80-byte gradient record and a 4-byte tile count,
+ * plus 24 bytes per unit of instance_capacity and 8 bytes per pixel. */
 size_t splat2d_workspace_size(const splat2d_config* cfg, const splat2d_problem* prob);
 
 /*
@@ -199,6 +202,23 @@ int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, c
                        void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth,
                        const float* d_normal, const float* d_alpha, const splat2d_grads* grads,
                        splat2d_stream stream);
+
+/*
+ * The two halves of splat2d_render_bwd, for callers that time or overlap
+ * them separately: the tile adjoint leaves per-(view, surfel) record
+ * gradients in `ws`; the chain rule turns them into parameter and pose
+ * gradients (accumulated into `grads`).  Calling both in this order is
+ * exactly splat2d_render_bwd.
+ */
+int splat2d_render_bwd_tiles(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                             const float* d_rgb, const float* d_depth, const float* d_normal, const float* d_alpha,
+                             splat2d_stream stream);
+int splat2d_preprocess_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                           void* ws, size_t ws_bytes, const splat2d_grads* grads, splat2d_stream stream);
+
+/* Number of kernels this library has enqueued since it was loaded (host-side
+ * count, including launches recorded into a CUDA graph). */
+uint64_t splat2d_launch_count(void);
 
 /* Synchronise `stream`, read the device status and counters of the last
  * iteration into *out.  Returns out->status (or a host error). */

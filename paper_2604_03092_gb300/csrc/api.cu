@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -10,6 +11,12 @@
 #include "splat2d_internal.cuh"
 
 namespace s2d {
+
+std::atomic<uint64_t>& launch_counter() {
+  static std::atomic<uint64_t> c{0};
+  return c;
+}
+void count_launches(int n) { launch_counter().fetch_add((uint64_t)n); }
 
 int sm_count() {
   static int cached[64] = {0};
@@ -296,22 +303,48 @@ int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, v
   return SPLAT2D_OK;
 }
 
-int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
-                       void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
-                       const float* d_alpha, const splat2d_grads* grads, splat2d_stream stream) {
+int splat2d_render_bwd_tiles(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                             const float* d_rgb, const float* d_depth, const float* d_normal, const float* d_alpha,
+                             splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
+  if (launch_render_bwd(L, make_params(cfg), cfg->chunk, w, vals, d_rgb, d_depth, d_normal, d_alpha, st) !=
+      cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_preprocess_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                           void* ws, size_t ws_bytes, const splat2d_grads* grads, splat2d_stream stream) {
   Layout L;
   int rc = check_common(cfg, prob, ws, ws_bytes, &L);
   if (rc) return rc;
   if (!surfels || surfels->n != prob->n_surfels || !grads) return SPLAT2D_ERR_INVALID_ARG;
+  if (prob->n_surfels > 0 && (!surfels->means || !surfels->scales || !surfels->quats || !surfels->opacity ||
+                              !surfels->rgb))
+    return SPLAT2D_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(surfels->quats) & 15) return SPLAT2D_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  char* w = static_cast<char*>(ws);
-  const RastParams P = make_params(cfg);
-  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
-  if (launch_render_bwd(L, P, cfg->chunk, w, vals, d_rgb, d_depth, d_normal, d_alpha, st) != cudaSuccess)
+  if (launch_preprocess_bwd(surfels, L, make_params(cfg), static_cast<char*>(ws), grads, L.groups_overlap, st) !=
+      cudaSuccess)
     return SPLAT2D_ERR_CUDA;
-  if (launch_preprocess_bwd(surfels, L, P, w, grads, L.groups_overlap, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
   return SPLAT2D_OK;
 }
+
+int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                       void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
+                       const float* d_alpha, const splat2d_grads* grads, splat2d_stream stream) {
+  if (!surfels || !prob || surfels->n != prob->n_surfels || !grads) return SPLAT2D_ERR_INVALID_ARG;
+  int rc = splat2d_render_bwd_tiles(cfg, prob, ws, ws_bytes, d_rgb, d_depth, d_normal, d_alpha, stream);
+  if (rc) return rc;
+  return splat2d_preprocess_bwd(cfg, prob, surfels, ws, ws_bytes, grads, stream);
+}
+
+uint64_t splat2d_launch_count(void) { return s2d::launch_counter().load(); }
 
 int splat2d_stats(const void* ws, splat2d_stats_t* out, splat2d_stream stream) {
   if (!ws || !out) return SPLAT2D_ERR_INVALID_ARG;

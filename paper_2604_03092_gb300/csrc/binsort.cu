@@ -170,7 +170,9 @@ cudaError_t launch_bin(const Layout& L, const RastParams& P, char* ws, cudaStrea
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
   int grid = (int)min64(L.n_scan_tiles, (int64_t)sm_count() * 8);
   k_scan_reduce<<<grid, 256, 0, st>>>(ntiles, L.R, part, L.n_scan_tiles);
+  count_launches(1);
   k_scan_partials<<<1, 1024, 0, st>>>(part, L.n_scan_tiles, hdr, L.cap);
+  count_launches(1);
   BinArgs A;
   A.ntiles = ntiles;
   A.records = reinterpret_cast<const float4*>(ws + L.records);
@@ -185,6 +187,7 @@ cudaError_t launch_bin(const Layout& L, const RastParams& P, char* ws, cudaStrea
   A.keys = reinterpret_cast<uint64_t*>(ws + L.keys0);
   A.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
   k_bin<<<grid, 256, 0, st>>>(A);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -341,9 +344,12 @@ cudaError_t launch_sort(uint64_t* keys0, uint32_t* vals0, uint64_t* keys1, uint3
   int cur = 0;
   for (int shift = 0; shift < key_bits; shift += 8) {
     k_sort_upsweep<<<sort_blocks, SORT_THREADS, 0, st>>>(kb[cur], n_dev, n_max, shift, hist);
+    count_launches(1);
     k_sort_scan<<<256, 1024, 0, st>>>(hist, sort_blocks);
+    count_launches(1);
     k_sort_downsweep<<<sort_blocks, SORT_THREADS, 0, st>>>(kb[cur], vb[cur], kb[cur ^ 1], vb[cur ^ 1], n_dev,
                                                            n_max, shift, hist);
+    count_launches(1);
     cur ^= 1;
   }
   *final_buffer = cur;
@@ -412,6 +418,7 @@ cudaError_t launch_ranges(const Layout& L, const uint64_t* keys, char* ws, cudaS
   int grid = (int)min64((L.cap + 255) / 256, (int64_t)sm_count() * 8);
   if (grid < 1) grid = 1;
   k_ranges<<<grid, 256, 0, st>>>(keys, &hdr->n_inst, ranges);
+  count_launches(1);
   uint32_t* bins = reinterpret_cast<uint32_t*>(ws + L.tile_hist);
   uint32_t* order = reinterpret_cast<uint32_t*>(ws + L.tile_order);
   e = cudaMemsetAsync(bins, 0, sizeof(uint32_t) * ORDER_BINS, st);
@@ -419,8 +426,11 @@ cudaError_t launch_ranges(const Layout& L, const uint64_t* keys, char* ws, cudaS
   int g2 = (int)min64((L.T + 255) / 256, (int64_t)sm_count() * 4);
   if (g2 < 1) g2 = 1;
   k_order_hist<<<g2, 256, 0, st>>>(ranges, L.T, bins);
+  count_launches(1);
   k_order_scan<<<1, 32, 0, st>>>(bins);
+  count_launches(1);
   k_order_scatter<<<g2, 256, 0, st>>>(ranges, L.T, bins, order);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -44,6 +44,7 @@ cudaError_t launch_upload(const void* host_src, size_t bytes, void* dst, cudaStr
     memset(&blob, 0, sizeof(blob));
     memcpy(&blob, src + off, n);
     k_upload<<<1, 256, 0, st>>>(blob, reinterpret_cast<uint4*>(static_cast<char*>(dst) + off), (int)n16);
+    count_launches(1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -269,9 +270,6 @@ __global__ void __launch_bounds__(256) k_preprocess(const PreArgs A) {
         float4* dst = A.records + rec * REC_F4;
 #pragma unroll
         for (int k = 0; k < REC_F4; k++) dst[k] = r[k];
-        float4* gd = A.rgrad + rec * (GRAD_F / 4);
-#pragma unroll
-        for (int k = 0; k < GRAD_F / 4; k++) gd[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         vis++;
       }
     }
@@ -300,6 +298,7 @@ cudaError_t launch_preprocess(const splat2d_surfels* S, const Layout& L, const R
   int64_t cap = (int64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
   k_preprocess<<<(unsigned)blocks, 256, 0, st>>>(A);
+  count_launches(1);
   return cudaGetLastError();
 }
 
@@ -315,7 +314,7 @@ struct PreBwdArgs {
   int64_t per_block;   // contiguous work items per block
   RastParams P;
   const uint32_t* ntiles;
-  const float4* rgrad;
+  float4* rgrad;  // consumed and cleared: zero again when this kernel ends
   splat2d_grads out;
   int32_t atomic_params;
 };
@@ -357,8 +356,17 @@ __global__ void __launch_bounds__(256) k_preprocess_bwd(const PreBwdArgs A) {
         const DView& vw = A.views[v];
         const int64_t rec = vw.rbase + (s - vw.soff);
         if (A.ntiles[rec]) {
-          const float4* gp = A.rgrad + rec * (GRAD_F / 4);
+          float4* gp = A.rgrad + rec * (GRAD_F / 4);
           const float4 q0 = gp[0], q1 = gp[1], q2 = gp[2], q3 = gp[3], q4 = gp[4];
+          // leave the gradient record zero for the next reverse pass
+          const bool touched = (q0.x != 0.f) | (q0.y != 0.f) | (q0.z != 0.f) | (q0.w != 0.f) | (q1.x != 0.f) |
+                               (q1.y != 0.f) | (q1.z != 0.f) | (q1.w != 0.f) | (q2.x != 0.f) | (q2.y != 0.f) |
+                               (q2.z != 0.f) | (q2.w != 0.f) | (q3.x != 0.f) | (q3.y != 0.f) | (q3.z != 0.f) |
+                               (q3.w != 0.f) | (q4.x != 0.f);
+          if (touched) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            gp[0] = z; gp[1] = z; gp[2] = z; gp[3] = z; gp[4] = z;
+          }
           const float gr[17] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x,
                                 q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w, q4.x};
           // camera frame (FP32 is enough for the chain rule)
@@ -516,7 +524,7 @@ cudaError_t launch_preprocess_bwd(const splat2d_surfels* S, const Layout& L, con
   A.n_work = n_work;
   A.P = P;
   A.ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
-  A.rgrad = reinterpret_cast<const float4*>(ws + L.rgrad);
+  A.rgrad = reinterpret_cast<float4*>(ws + L.rgrad);
   A.out = *G;
   A.atomic_params = atomic_params ? 1 : 0;
   int64_t blocks_cap = (int64_t)sm_count() * 8;
@@ -526,6 +534,7 @@ cudaError_t launch_preprocess_bwd(const splat2d_surfels* S, const Layout& L, con
   A.per_block = per;
   int64_t blocks = (n_work + per - 1) / per;
   k_preprocess_bwd<<<(unsigned)blocks, 256, 0, st>>>(A);
+  count_launches(1);
   return cudaGetLastError();
 }
 

@@ -472,6 +472,7 @@ static cudaError_t run_fwd(const RenderArgs& A, cudaStream_t st) {
     grid_T = A.T;
   }
   k<<<grid, TW * TH, 0, st>>>(A);
+  count_launches(1);
   return cudaGetLastError();
 }
 template <int TW, int TH, int CHUNK>
@@ -484,6 +485,7 @@ static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
     grid_T = A.T;
   }
   k<<<grid, TW * TH, 0, st>>>(A);
+  count_launches(1);
   return cudaGetLastError();
 }
 

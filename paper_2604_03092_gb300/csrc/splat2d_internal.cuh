@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "splat2d.h"
 
 namespace s2d {
@@ -108,6 +110,7 @@ __host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return
 
 // Host helpers (api.cu)
 bool compute_layout(const splat2d_config* cfg, const splat2d_problem* prob, Layout* L);
+std::atomic<uint64_t>& launch_counter();
 
 // Per-launch constants
 struct RastParams {
@@ -138,6 +141,7 @@ cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, c
 cudaError_t launch_preprocess_bwd(const splat2d_surfels* S, const Layout& L, const RastParams& P, char* ws,
                                   const splat2d_grads* G, bool atomic_params, cudaStream_t st);
 int sm_count();
+void count_launches(int n);  // host-side tally of kernels enqueued
 
 // ---------------------------------------------------------------------------
 // Device helpers

@@ -140,7 +140,8 @@ class Rasterizer:
             raise ValueError("invalid rasterizer problem (check views, surfel ranges and the config)")
         self.ws_bytes = int(size)
         self.ws = None
-        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        # zero-filled once: the library keeps its gradient records zero between iterations
+        self.ws = torch.zeros(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
         base = self.ws.data_ptr()
         self._ws_ptr = (base + 255) & ~255
         lay = _abi.Layout()
@@ -223,6 +224,26 @@ class Rasterizer:
         _abi.check(self.lib.splat2d_render_bwd(ctypes.byref(self._cfg), ctypes.byref(self._prob), ctypes.byref(sf),
                                                self._ws_ptr, self.ws_bytes, d[0], d[1], d[2], d[3], ctypes.byref(g),
                                                _stream()), "splat2d_render_bwd")
+
+    def render_bwd_tiles(self, d_out: Sequence[Optional[torch.Tensor]]):
+        """Tile adjoint only: record gradients stay in the workspace."""
+        d = [None if t is None else _ptr(t) for t in d_out]
+        _abi.check(self.lib.splat2d_render_bwd_tiles(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
+                                                     self.ws_bytes, d[0], d[1], d[2], d[3], _stream()),
+                   "splat2d_render_bwd_tiles")
+
+    def preprocess_bwd(self, means, scales, quats, opacity, rgb, grads: SurfelGrads):
+        """Chain rule from the workspace's record gradients to `grads`."""
+        sf = self._surfels(means, scales, quats, opacity, rgb)
+        g = _abi.Grads()
+        g.means, g.scales, g.quats = _ptr(grads.means), _ptr(grads.scales), _ptr(grads.quats)
+        g.opacity, g.rgb, g.pose = _ptr(grads.opacity), _ptr(grads.rgb), _ptr(grads.pose)
+        _abi.check(self.lib.splat2d_preprocess_bwd(ctypes.byref(self._cfg), ctypes.byref(self._prob), ctypes.byref(sf),
+                                                   self._ws_ptr, self.ws_bytes, ctypes.byref(g), _stream()),
+                   "splat2d_preprocess_bwd")
+
+    def launch_count(self) -> int:
+        return int(self.lib.splat2d_launch_count())
 
     def stats(self) -> dict:
         """Synchronises; device status and pair counters of the last iteration."""
