@@ -56,6 +56,8 @@ def _workloads():
     return {
         "submap32": ("32 keyframes x 512x384 = 6,291,456 surfels, 32 views at 512x384 (fx=fy=400), 3-room layout",
                      lambda seed: scenes.submap_scene(seed=2001 + seed)),
+        "submap8": ("8 keyframes x 512x384 = 1,572,864 surfels, 8 views at 512x384 (a smaller submap for profiling)",
+                    lambda seed: scenes.submap_scene(seed=2001 + seed, n_keyframes=8)),
         "keyframe8": ("one 512x384 keyframe = 196,608 surfels, 8 perturbed views at 512x384",
                       lambda seed: scenes.keyframe_scene(seed=1001 + seed)),
         "random4096": ("4,096 random surfels, one 128x96 view",
