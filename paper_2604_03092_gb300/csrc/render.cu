@@ -3,19 +3,22 @@
 // Both kernels are persistent: one CTA per tile-shaped block of pixels pulls
 // (view, tile) work items from an atomic queue ordered longest list first,
 // so many views of uneven size run in one launch.  A tile's sorted surfel
-// list is staged through shared memory in chunks; while staging, each entry's
-// pixel rect is tested against every warp's 8x4 pixel patch and the result is
-// kept as one bit per (warp, entry), so a warp only visits entries that can
-// reach its pixels.
+// list is staged through shared memory in chunks.  For each chunk every lane
+// (one pixel) gets a bitmask of the chunk entries whose pixel rect holds its
+// pixel, built with 12 ballots per 32 entries (which entries span each column
+// and each row of the warp's 8x4 patch), and then walks only its own entries:
+// surfels are a few pixels wide, so a lane-per-pixel walk over a shared entry
+// sequence would leave most lanes idle, while here nearly every lane does a
+// useful (pixel, surfel) evaluation on every step.
 //
-// Forward (Eq. 1): front to back, alpha = min(alpha_max, sigma * G), pairs
-// below alpha_min skipped, stop before T would fall below t_min; the warp
-// leaves the chunk as soon as all its pixels have stopped.
-// Backward: back to front from each pixel's last blended entry, T recovered
+// Forward (Eq. 1): front to back per pixel, alpha = min(alpha_max, sigma*G),
+// pairs below alpha_min skipped, stop before T would fall below t_min; the
+// tile stops staging as soon as all its pixels have stopped.
+// Backward: back to front per pixel from its last blended entry, T recovered
 // by division, one scalar suffix sum per pixel (the upstream gradient dotted
-// with the features of the entries behind), per-entry gradients summed across
-// the warp by a transposing butterfly (16 values in 16 shuffles), across the
-// CTA in shared memory, then one set of vector atomics per (tile, entry).
+// with the features of the entries behind); each lane adds its pair's
+// gradient to the entry's shared-memory slot, and after the chunk one set of
+// vector atomics per (tile, entry) moves the sums to the gradient record.
 #include <cuda_runtime.h>
 
 #include "splat2d_internal.cuh"
@@ -98,44 +101,55 @@ struct RenderArgs {
   const float* d_alpha;
 };
 
-// Stage entries [base, base + count) of the sorted list into shared memory
-// and build the per-warp visit masks.
-template <int TW, int TH, int CHUNK>
+// Stage entries [base, base + count) of the sorted list into shared memory.
+template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                            int tx0, int ty0, SRec* s_rec, uint32_t* s_mask, uint32_t* s_idx) {
-  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int jb = wid * 32; jb < CHUNK; jb += NT) {
-    const int j = jb + lane;
-    uint32_t m = 0;
-    if (j < count) {
-      const uint32_t s = __ldg(A.vals + base + j);
-      const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
-      SRec r;
-      unpack_record(A.records + rec * REC_F4, r);
-      s_rec[j] = r;
-      if (s_idx) s_idx[j] = (uint32_t)rec;
-#pragma unroll
-      for (int w = 0; w < NW; w++) {
-        const int bx = tx0 + (w % WX) * 8, by = ty0 + (w / WX) * 4;
-        const bool hit = r.rect.x <= bx + 7 && r.rect.x + r.rect.z >= bx && r.rect.y <= by + 3 &&
-                         r.rect.y + r.rect.w >= by;
-        m |= (uint32_t)hit << w;
-      }
-    }
-#pragma unroll
-    for (int w = 0; w < NW; w++) {
-      const uint32_t bal = __ballot_sync(0xffffffffu, (m >> w) & 1u);
-      if (lane == 0) s_mask[w * (CHUNK / 32) + (jb >> 5)] = bal;
-    }
+                                            SRec* s_rec, uint32_t* s_idx) {
+  for (int j = threadIdx.x; j < count; j += NT) {
+    const uint32_t s = __ldg(A.vals + base + j);
+    const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
+    unpack_record(A.records + rec * REC_F4, s_rec[j]);
+    if (s_idx) s_idx[j] = (uint32_t)rec;
   }
 }
 
+// Per-lane visit masks.  Each warp owns an 8x4 pixel patch (lane = column
+// (lane & 7), row (lane >> 3)).  For the 32 entries of word `wd` of the chunk,
+// returns the bits of the entries whose pixel rect holds this lane's pixel:
+// the warp ballots, per patch column and per patch row, which entries'
+// rects span it, and each lane ANDs its column's and its row's ballot.
+__device__ __forceinline__ uint32_t lane_word(const SRec* s_rec, int wd, int count, int bx, int by, int lane) {
+  const int j = wd * 32 + lane;
+  uint32_t cm = 0, rm = 0;
+  if (j < count) {
+    const int4 r = s_rec[j].rect;  // x0, y0, x1 - x0, y1 - y0
+    const int c0 = max(r.x - bx, 0), c1 = min(r.x + r.z - bx, 7);
+    const int r0 = max(r.y - by, 0), r1 = min(r.y + r.w - by, 3);
+    if (c0 <= c1 && r0 <= r1) {
+      cm = ((2u << c1) - 1u) & ~((1u << c0) - 1u);
+      rm = ((2u << r1) - 1u) & ~((1u << r0) - 1u);
+    }
+  }
+  uint32_t colb[8], rowb[4];
+#pragma unroll
+  for (int c = 0; c < 8; c++) colb[c] = __ballot_sync(0xffffffffu, (cm >> c) & 1u);
+#pragma unroll
+  for (int r = 0; r < 4; r++) rowb[r] = __ballot_sync(0xffffffffu, (rm >> r) & 1u);
+  const int mc = lane & 7, mr = lane >> 3;
+  uint32_t cw = colb[0];
+#pragma unroll
+  for (int c = 1; c < 8; c++) cw = (mc == c) ? colb[c] : cw;
+  uint32_t rw = rowb[0];
+#pragma unroll
+  for (int r = 1; r < 4; r++) rw = (mr == r) ? rowb[r] : rw;
+  return cw & rw;
+}
+
 template <int TW, int TH, int CHUNK>
-__global__ void __launch_bounds__(TW* TH) k_render_fwd(const RenderArgs A) {
-  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd(const RenderArgs A) {
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
   __shared__ SRec s_rec[CHUNK];
-  __shared__ uint32_t s_mask[NW * (CHUNK / 32)];
+  __shared__ uint32_t s_bits[NW][NWD][32];
   __shared__ int s_item;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const RastParams& P = A.P;
@@ -151,8 +165,8 @@ __global__ void __launch_bounds__(TW* TH) k_render_fwd(const RenderArgs A) {
     const DView& vw = A.views[v];
     const int lt = t - vw.tile_base;
     const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
-    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7);
-    const int ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
+    const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
+    const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
     const bool inside = ipx < vw.W && ipy < vw.H;
     const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
@@ -162,41 +176,42 @@ __global__ void __launch_bounds__(TW* TH) k_render_fwd(const RenderArgs A) {
     for (int64_t base = range.x; base < range.y; base += CHUNK) {
       if (__syncthreads_count(!done) == 0) break;
       const int count = (int)min64(CHUNK, (int64_t)range.y - base);
-      stage_chunk<TW, TH, CHUNK>(A, vw, base, count, tx0, ty0, s_rec, s_mask, nullptr);
+      stage_chunk<NT, CHUNK>(A, vw, base, count, s_rec, nullptr);
       __syncthreads();
-      if (!__all_sync(0xffffffffu, done)) {
-        for (int wd = 0; wd < CHUNK / 32; wd++) {
-          uint32_t bits = s_mask[wid * (CHUNK / 32) + wd];
-          while (bits) {
-            const int j = wd * 32 + __ffs(bits) - 1;
-            bits &= bits - 1;
-            if (done) continue;
-            const int4 rc = s_rec[j].rect;
-            if (!in_rect(rc, ipx, ipy)) continue;
-            Pair e;
-            eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
-            n_eval++;
-            if (e.alpha < P.alpha_min) continue;
-            const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-            if (Tn < P.t_min) {
-              done = true;
-              continue;
-            }
-            const float w = __fmul_rn(e.alpha, T);
-            const float4 col = s_rec[j].col, nrm = s_rec[j].n;
-            C0 = __fmaf_rn(w, col.x, C0);
-            C1 = __fmaf_rn(w, col.y, C1);
-            C2 = __fmaf_rn(w, col.z, C2);
-            D = __fmaf_rn(w, col.w, D);
-            N0 = __fmaf_rn(w, nrm.x, N0);
-            N1 = __fmaf_rn(w, nrm.y, N1);
-            N2 = __fmaf_rn(w, nrm.z, N2);
-            T = Tn;
-            last = (uint32_t)(base + j + 1);
-            n_blend++;
-          }
-          if (__all_sync(0xffffffffu, done)) break;
+      if (__all_sync(0xffffffffu, done)) continue;
+      const int nwd = (count + 31) >> 5;
+      for (int wd = 0; wd < nwd; wd++) s_bits[wid][wd][lane] = lane_word(s_rec, wd, count, bx, by, lane);
+      // each lane walks its own pixel's entries, front to back
+      int wd = 0;
+      uint32_t b = done ? 0u : s_bits[wid][0][lane];
+      for (;;) {
+        while (b == 0 && !done && wd + 1 < nwd) b = s_bits[wid][++wd][lane];
+        const bool has = b != 0 && !done;
+        if (!__any_sync(0xffffffffu, has)) break;
+        if (!has) continue;
+        const int j = wd * 32 + __ffs(b) - 1;
+        b &= b - 1;
+        Pair e;
+        eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
+        n_eval++;
+        if (e.alpha < P.alpha_min) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
+        if (Tn < P.t_min) {
+          done = true;
+          continue;
         }
+        const float w = __fmul_rn(e.alpha, T);
+        const float4 col = s_rec[j].col, nrm = s_rec[j].n;
+        C0 = __fmaf_rn(w, col.x, C0);
+        C1 = __fmaf_rn(w, col.y, C1);
+        C2 = __fmaf_rn(w, col.z, C2);
+        D = __fmaf_rn(w, col.w, D);
+        N0 = __fmaf_rn(w, nrm.x, N0);
+        N1 = __fmaf_rn(w, nrm.y, N1);
+        N2 = __fmaf_rn(w, nrm.z, N2);
+        T = Tn;
+        last = (uint32_t)(base + j + 1);
+        n_blend++;
       }
     }
     if (inside) {
@@ -221,60 +236,66 @@ __global__ void __launch_bounds__(TW* TH) k_render_fwd(const RenderArgs A) {
     }
   }
   if (P.stats) {
-    unsigned long long a = n_eval, b = n_blend;
+    unsigned long long a = n_eval, bb = n_blend;
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
+      bb += __shfl_xor_sync(0xffffffffu, bb, o);
     }
     if (lane == 0) {
       atomicAdd(&A.hdr->stat[STAT_FWD_EVAL], a);
-      atomicAdd(&A.hdr->stat[STAT_FWD_BLEND], b);
+      atomicAdd(&A.hdr->stat[STAT_FWD_BLEND], bb);
     }
   }
-}
-
-// Sum 16 per-lane values over the warp; afterwards lane L (and L ^ 1) holds
-// the total of value index (L >> 1) & 15 in v[0].
-__device__ __forceinline__ void warp_transpose_sum16(float (&v)[16], int lane) {
-#pragma unroll
-  for (int i = 0; i < 8; i++) {
-    const bool up = lane & 16;
-    const float send = up ? v[i] : v[i + 8];
-    const float keep = up ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; i++) {
-    const bool up = lane & 8;
-    const float send = up ? v[i] : v[i + 4];
-    const float keep = up ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; i++) {
-    const bool up = lane & 4;
-    const float send = up ? v[i] : v[i + 2];
-    const float keep = up ? v[i + 2] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  {
-    const bool up = lane & 2;
-    const float send = up ? v[0] : v[1];
-    const float keep = up ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 constexpr int SGRAD_STRIDE = 17;
 
+// Gradient of one kept (pixel, entry) pair w.r.t. the 16 stored record
+// quantities (G_* order) and the depth; `da` is dL/dalpha.
+__device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const float4 qq, float da, float w,
+                                           float dC0, float dC1, float dC2, float dD, float dN0, float dN1,
+                                           float dN2, float lp_scale, float (&g)[16], float& gz) {
+#pragma unroll
+  for (int k = 0; k < 16; k++) g[k] = 0.f;
+  g[G_R] = w * dC0;
+  g[G_G] = w * dC1;
+  g[G_B] = w * dC2;
+  gz = w * dD;
+  g[G_NX] = w * dN0;
+  g[G_NY] = w * dN1;
+  g[G_NZ] = w * dN2;
+  if (!e.clamped) {
+    g[G_OP] = da * e.G;
+    const float drho = -kLn2 * e.G * (da * qq.w);
+    float ddx, ddy;
+    if (e.obj) {
+      const float t2 = 2.f * drho * e.rc * e.rc;
+      const float gA = t2 * e.a, gB = t2 * e.b, gC = -2.f * drho * e.rho * e.rc;
+      g[G_P00] = gA * e.dx;
+      g[G_P01] = gA * e.dy;
+      g[G_P10] = gB * e.dx;
+      g[G_P11] = gB * e.dy;
+      g[G_P20] = gC * e.dx;
+      g[G_P21] = gC * e.dy;
+      g[G_P22] = gC;
+      ddx = gA * pp.x + gB * pp.z + gC * qq.x;
+      ddy = gA * pp.y + gB * pp.w + gC * qq.y;
+    } else {
+      ddx = 2.f * lp_scale * e.dx * drho;
+      ddy = 2.f * lp_scale * e.dy * drho;
+    }
+    g[G_CX] = -ddx;
+    g[G_CY] = -ddy;
+  }
+}
+
 template <int TW, int TH, int CHUNK>
-__global__ void __launch_bounds__(TW* TH) k_render_bwd(const RenderArgs A) {
-  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(const RenderArgs A) {
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
   __shared__ SRec s_rec[CHUNK];
-  __shared__ uint32_t s_mask[NW * (CHUNK / 32)];
   __shared__ uint32_t s_idx[CHUNK];
   __shared__ float s_grad[CHUNK * SGRAD_STRIDE];
+  __shared__ uint32_t s_bits[NW][NWD][32];
   __shared__ int s_item;
   __shared__ uint32_t s_top;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -291,12 +312,11 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const RenderArgs A) {
     const DView& vw = A.views[v];
     const int lt = t - vw.tile_base;
     const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
-    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7);
-    const int ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
+    const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
+    const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
     const bool inside = ipx < vw.W && ipy < vw.H;
     const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
-    // per-pixel state
     const int64_t HW = (int64_t)vw.W * vw.H;
     const int64_t pix = (int64_t)ipy * vw.W + ipx;
     uint32_t my_last = range.x;
@@ -326,74 +346,49 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const RenderArgs A) {
     for (int64_t hi = top; hi > (int64_t)range.x; hi -= CHUNK) {
       const int64_t lo = max64((int64_t)range.x, hi - CHUNK);
       const int count = (int)(hi - lo);
-      stage_chunk<TW, TH, CHUNK>(A, vw, lo, count, tx0, ty0, s_rec, s_mask, s_idx);
+      stage_chunk<NT, CHUNK>(A, vw, lo, count, s_rec, s_idx);
       __syncthreads();
-      for (int wd = CHUNK / 32 - 1; wd >= 0; wd--) {
-        uint32_t bits = s_mask[wid * (CHUNK / 32) + wd];
-        while (bits) {
-          const int jj = 31 - __clz(bits);
-          bits &= ~(1u << jj);
+      const int lim = (int)min64((int64_t)my_last - lo, count);  // entries below this pixel's last
+      if (__any_sync(0xffffffffu, lim > 0)) {
+        const int nwd = (count + 31) >> 5;
+        for (int wd = 0; wd < nwd; wd++) {
+          uint32_t m = lane_word(s_rec, wd, count, bx, by, lane);
+          const int keep = lim - wd * 32;
+          m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
+          s_bits[wid][wd][lane] = m;
+        }
+        // each lane walks its own pixel's entries, back to front
+        int wd = nwd - 1;
+        uint32_t b = s_bits[wid][wd][lane];
+        for (;;) {
+          while (b == 0 && wd > 0) b = s_bits[wid][--wd][lane];
+          const bool has = b != 0;
+          if (!__any_sync(0xffffffffu, has)) break;
+          if (!has) continue;
+          const int jj = 31 - __clz(b);
+          b &= ~(1u << jj);
           const int j = wd * 32 + jj;
-          const uint32_t i = (uint32_t)(lo + j);
-          bool act = false;
           Pair e;
-          const int4 rc = s_rec[j].rect;
-          if (i < my_last && in_rect(rc, ipx, ipy)) {
-            eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
-            n_eval++;
-            act = e.alpha >= P.alpha_min;
-          }
-          if (!__any_sync(0xffffffffu, act)) continue;
+          eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
+          n_eval++;
+          if (e.alpha < P.alpha_min) continue;
+          n_blend++;
+          const float4 col = s_rec[j].col, nrm = s_rec[j].n;
+          const float iom = rcp_approx(__fsub_rn(1.f, e.alpha));
+          const float Ti = T * iom;
+          const float w = e.alpha * Ti;
+          const float f = fmaf(dC0, col.x, fmaf(dC1, col.y, fmaf(dC2, col.z, fmaf(dD, col.w,
+                          fmaf(dN0, nrm.x, fmaf(dN1, nrm.y, dN2 * nrm.z))))));
+          const float da = Ti * f - (Q - dAT) * iom;
+          Q = fmaf(w, f, Q);
+          T = Ti;
           float g[16];
-          float gz = 0.f;
+          float gz;
+          pair_grads(e, s_rec[j].p, s_rec[j].q, da, w, dC0, dC1, dC2, dD, dN0, dN1, dN2, P.lp_scale, g, gz);
+          float* sg = s_grad + j * SGRAD_STRIDE;
 #pragma unroll
-          for (int k = 0; k < 16; k++) g[k] = 0.f;
-          if (act) {
-            n_blend++;
-            const float4 col = s_rec[j].col, nrm = s_rec[j].n, pp = s_rec[j].p, qq = s_rec[j].q;
-            const float iom = rcp_approx(__fsub_rn(1.f, e.alpha));
-            const float Ti = T * iom;
-            const float w = e.alpha * Ti;
-            const float f = fmaf(dC0, col.x, fmaf(dC1, col.y, fmaf(dC2, col.z, fmaf(dD, col.w,
-                            fmaf(dN0, nrm.x, fmaf(dN1, nrm.y, dN2 * nrm.z))))));
-            const float da = Ti * f - (Q - dAT) * iom;
-            Q = fmaf(w, f, Q);
-            T = Ti;
-            g[G_R] = w * dC0;
-            g[G_G] = w * dC1;
-            g[G_B] = w * dC2;
-            gz = w * dD;
-            g[G_NX] = w * dN0;
-            g[G_NY] = w * dN1;
-            g[G_NZ] = w * dN2;
-            if (!e.clamped) {
-              g[G_OP] = da * e.G;
-              const float drho = -kLn2 * e.G * (da * qq.w);
-              float ddx, ddy;
-              if (e.obj) {
-                const float t2 = 2.f * drho * e.rc * e.rc;
-                const float gA = t2 * e.a, gB = t2 * e.b, gC = -2.f * drho * e.rho * e.rc;
-                g[G_P00] = gA * e.dx;
-                g[G_P01] = gA * e.dy;
-                g[G_P10] = gB * e.dx;
-                g[G_P11] = gB * e.dy;
-                g[G_P20] = gC * e.dx;
-                g[G_P21] = gC * e.dy;
-                g[G_P22] = gC;
-                ddx = gA * pp.x + gB * pp.z + gC * qq.x;
-                ddy = gA * pp.y + gB * pp.w + gC * qq.y;
-              } else {
-                ddx = 2.f * P.lp_scale * e.dx * drho;
-                ddy = 2.f * P.lp_scale * e.dy * drho;
-              }
-              g[G_CX] = -ddx;
-              g[G_CY] = -ddy;
-            }
-          }
-          warp_transpose_sum16(g, lane);
-          for (int o = 16; o > 0; o >>= 1) gz += __shfl_xor_sync(0xffffffffu, gz, o);
-          if ((lane & 1) == 0) atomicAdd(&s_grad[j * SGRAD_STRIDE + (lane >> 1)], g[0]);
-          if (lane == 1) atomicAdd(&s_grad[j * SGRAD_STRIDE + 16], gz);
+          for (int k = 0; k < 16; k++) atomicAdd(sg + k, g[k]);
+          atomicAdd(sg + 16, gz);
         }
       }
       __syncthreads();
@@ -418,14 +413,14 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(const RenderArgs A) {
     }
   }
   if (P.stats) {
-    unsigned long long a = n_eval, b = n_blend;
+    unsigned long long a = n_eval, bb = n_blend;
     for (int o = 16; o > 0; o >>= 1) {
       a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
+      bb += __shfl_xor_sync(0xffffffffu, bb, o);
     }
     if (lane == 0) {
       atomicAdd(&A.hdr->stat[STAT_BWD_EVAL], a);
-      atomicAdd(&A.hdr->stat[STAT_BWD_BLEND], b);
+      atomicAdd(&A.hdr->stat[STAT_BWD_BLEND], bb);
     }
   }
 }
