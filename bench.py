@@ -423,7 +423,7 @@ def main():
     passes = (32 + max(int(lay.n_tiles - 1).bit_length(), 0) + 7) // 8
     work = {
         "preprocess": ("hbm", 56 * sum(1 for _ in [0]) * rast.n_surfels + 4 * lay.n_records + 160 * n_vis),
-        "bin_sort": ("hbm", 8 * lay.n_records + 16 * n_vis + 12 * n_inst + passes * 32 * n_inst + 8 * n_inst),
+        "bin_sort": ("hbm", 8 * lay.n_records + 32 * n_vis + 8 * n_inst + 20 * n_inst),
         "render_fwd": ("alu", FLOP_EVAL * st["fwd_pairs_evaluated"] + FLOP_BLEND * st["fwd_pairs_blended"]),
         "render_bwd": ("alu", FLOP_EVAL * st["bwd_pairs_evaluated"] + FLOP_BWD * st["bwd_pairs_blended"]),
         "preprocess_bwd": ("hbm", 4 * lay.n_records + 80 * n_vis + 56 * rast.n_surfels + 52 * rast.n_surfels),

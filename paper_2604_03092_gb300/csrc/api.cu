@@ -136,7 +136,6 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->cap = prob->instance_capacity;
   L->n_work = work;
   L->groups_overlap = overlap;
-  L->n_scan_tiles = (R + SCAN_TILE - 1) / SCAN_TILE;
   L->sort_blocks = std::min(SORT_MAX_BLOCKS, 4 * sm_count());
   L->key_bits = key_bits_for(T);
   size_t off = 0;
@@ -151,15 +150,15 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->ntiles = take(sizeof(uint32_t) * R);
   L->records = take(sizeof(float4) * REC_F4 * R);
   L->rgrad = take(sizeof(float) * GRAD_F * R);
-  L->scan_part = take(sizeof(unsigned long long) * (L->n_scan_tiles + 1));
   L->keys0 = take(sizeof(uint64_t) * L->cap);
   L->keys1 = take(sizeof(uint64_t) * L->cap);
   L->vals0 = take(sizeof(uint32_t) * L->cap);
   L->vals1 = take(sizeof(uint32_t) * L->cap);
   L->sort_hist = take(sizeof(uint32_t) * (256 * (size_t)L->sort_blocks + 256));
   L->ranges = take(sizeof(uint2) * T);
+  L->tile_count = take(sizeof(uint32_t) * T);
   L->tile_order = take(sizeof(uint32_t) * T);
-  L->tile_hist = take(sizeof(uint32_t) * ORDER_BINS);
+  L->tile_hist = take(sizeof(uint32_t) * (ORDER_BINS + 8));
   L->tfinal = take(sizeof(float) * P);
   L->last = take(sizeof(uint32_t) * P);
   L->total = off;
@@ -195,7 +194,8 @@ static int check_common(const splat2d_config* cfg, const splat2d_problem* prob, 
   return SPLAT2D_OK;
 }
 
-static int final_sorted_buffer(const Layout& L) { return ((L.key_bits + 7) / 8) & 1; }
+// The binning leaves the sorted instances in buffer 0.
+static int final_sorted_buffer(const Layout&) { return 0; }
 
 }  // namespace s2d
 
@@ -273,20 +273,8 @@ int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, voi
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   RastParams P = make_params(cfg);
-  Header* hdr = reinterpret_cast<Header*>(w + L.header);
-  if (launch_bin(L, P, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
-  int fb = 0;
-  if (cudaMemsetAsync(w + L.sort_hist + sizeof(uint32_t) * 256 * (size_t)L.sort_blocks, 0, 256 * sizeof(uint32_t),
-                      st) != cudaSuccess)
-    return SPLAT2D_ERR_CUDA;
-  if (launch_sort(reinterpret_cast<uint64_t*>(w + L.keys0), reinterpret_cast<uint32_t*>(w + L.vals0),
-                  reinterpret_cast<uint64_t*>(w + L.keys1), reinterpret_cast<uint32_t*>(w + L.vals1), &hdr->n_inst,
-                  L.cap, L.key_bits, reinterpret_cast<uint32_t*>(w + L.sort_hist), L.sort_blocks, &fb,
-                  st) != cudaSuccess)
-    return SPLAT2D_ERR_CUDA;
-  if (L.cap > 0 && fb != final_sorted_buffer(L)) return SPLAT2D_ERR_CUDA;
-  const uint64_t* keys = reinterpret_cast<const uint64_t*>(w + (final_sorted_buffer(L) ? L.keys1 : L.keys0));
-  if (launch_ranges(L, keys, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  if (launch_bin_tiles(L, P, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
+  if (launch_order(L, w, st) != cudaSuccess) return SPLAT2D_ERR_CUDA;
   return SPLAT2D_OK;
 }
 

@@ -1,18 +1,19 @@
-// Tile binning and the device radix sort.
+// Tile binning and the device radix sorts.
 //
-// Binning: every visible (view, surfel) record emits one instance per tile of
-// its tile rect, in record order, with key = (global tile) << 32 | FP32 depth
-// bits and value = surfel index.  Offsets come from an exclusive scan of the
-// per-record tile counts (reduce -> scan of block sums -> scan + emit).
+// Binning (splat2d_bin_sort): every visible (view, surfel) record stands for
+// one instance per tile of its tile rect, with key = (global tile) << 32 |
+// FP32 depth bits and value = surfel index; the instances are ordered by key
+// with ties in ascending surfel index (= record order within a view), i.e.
+// exactly a stable sort of the keys in record order.  It is done as a radix
+// sort whose most significant digit is the whole tile index (count, scan,
+// scatter into per-tile buckets) followed by a least-significant-digit radix
+// sort of each bucket's depth bits in shared memory.
 //
-// Sort: least-significant-digit radix sort with 8-bit digits over the key bits
-// in use (32 depth bits + enough bits for the global tile index).  Each pass is
-// upsweep (per-block digit histograms) -> scan of the histograms -> downsweep
-// (stable ranking of each 2048-key tile with warp-level match, then scatter).
-// Blocks own contiguous, ordered slices of the input and every ranking step
-// preserves input order among equal digits, so the whole sort is stable:
-// instances with equal (tile, depth) keep ascending record order, i.e.
-// ascending surfel index within a view.
+// splat2d_sort_pairs: a general stable LSD radix sort of (u64 key, u32 value)
+// pairs with 8-bit digits over the key bits in use.  Each pass is upsweep
+// (per-block digit histograms) -> scan of the histograms -> downsweep (stable
+// ranking of each 2048-key tile with warp-level match, then scatter); blocks
+// own contiguous, ordered slices, so equal keys keep their input order.
 #include <cuda_runtime.h>
 
 #include "splat2d_internal.cuh"
@@ -20,44 +21,92 @@
 namespace s2d {
 
 // ---------------------------------------------------------------------------
-// exclusive scan of tile counts, fused with the emission of instances
+// Binning by tile: count -> scan -> scatter -> per-tile sort
+//
+// The first radix digit of the (tile, depth) key is the whole tile index: a
+// counting pass gives each tile's instance count (warp-aggregated atomics:
+// neighbouring surfels of a keyframe land in the same tiles), an exclusive
+// scan gives each tile's [start, end) range directly, and a scatter pass
+// drops every instance into its tile's bucket as a 64-bit composite
+// (depth bits << 32 | surfel index).  Then each tile's bucket is sorted on
+// its own by an LSD radix sort of the depth bits in shared memory (in global
+// memory for the rare buckets too large for shared memory), and equal depth
+// bits are put in ascending surfel index.  The result is the (tile, depth)
+// order with ties in surfel order -- the stable sort of the instance keys.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t* __restrict__ ntiles, int64_t R,
-                                                      unsigned long long* __restrict__ part, int64_t n_tiles) {
-  __shared__ unsigned long long s_w[8];
-  for (int64_t b = blockIdx.x; b < n_tiles; b += gridDim.x) {
-    const int64_t base = b * SCAN_TILE;
-    unsigned long long sum = 0;
-    for (int i = threadIdx.x; i < SCAN_TILE; i += 256) {
-      int64_t r = base + i;
-      if (r < R) sum += __ldg(ntiles + r);
+struct TileBinArgs {
+  const uint32_t* ntiles;
+  const float4* records;
+  const DView* views;
+  int32_t V;
+  int64_t R;
+  int32_t tile_w, tile_h;
+  uint32_t* counts;  // per tile; the scan turns them into scatter cursors
+  unsigned long long* bucket;
+  const Header* hdr;
+};
+
+// Visit every (record, tile) instance; warp lanes hold consecutive records and
+// walk their tile rects in step so equal tiles can be aggregated.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
+  if (SCATTER && A.hdr->status != 0) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += stride) {
+    const int64_t r = r0 + threadIdx.x;
+    const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
+    if (!__any_sync(0xffffffffu, nt != 0)) continue;
+    int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
+    uint64_t comp = 0;
+    if (nt) {
+      const int v = find_view_by_record(A.views, A.V, r);
+      const DView& vw = A.views[v];
+      const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
+      const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
+      tx0 = (int)(q0 & 0xffffu) / A.tile_w;
+      ty0 = (int)(q0 >> 16) / A.tile_h;
+      const int tx1 = (int)(q1 & 0xffffu) / A.tile_w;
+      w = tx1 - tx0 + 1;
+      tbase = vw.tile_base;
+      tilesx = vw.tiles_x;
+      comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
     }
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned long long t = 0;
-      for (int w = 0; w < 8; w++) t += s_w[w];
-      part[b] = t;
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
+    for (uint32_t k = 0; k < kmax; k++) {
+      const bool has = k < nt;
+      const uint32_t t = has ? (uint32_t)(tbase + (ty0 + (int)k / w) * tilesx + tx0 + (int)k % w) : 0xffffffffu;
+      const uint32_t peers = __match_any_sync(0xffffffffu, t);
+      if (!has) continue;
+      const int leader = __ffs(peers) - 1;
+      if (!SCATTER) {
+        if (lane == leader) atomicAdd(A.counts + t, (uint32_t)__popc(peers));
+      } else {
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(A.counts + t, (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        A.bucket[base + __popc(peers & lt_mask)] = comp;
+      }
     }
-    __syncthreads();
   }
 }
 
-// One block: exclusive scan of the block sums; total -> header, capacity check.
-__global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* __restrict__ part, int64_t n,
-                                                        Header* __restrict__ hdr, int64_t cap) {
+// One block: exclusive scan of the tile counts -> ranges, scatter cursors,
+// total and the capacity check.
+__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ counts, uint2* __restrict__ ranges,
+                                                    int64_t T, Header* __restrict__ hdr, int64_t cap) {
   __shared__ unsigned long long s_w[32];
   __shared__ unsigned long long s_carry;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
-  for (int64_t base = 0; base < n; base += 1024) {
-    int64_t i = base + threadIdx.x;
-    unsigned long long v = i < n ? part[i] : 0ull;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t base = 0; base < T; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const unsigned long long v = i < T ? counts[i] : 0ull;
     unsigned long long x = v;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
     if (lane == 31) s_w[wid] = x;
@@ -65,20 +114,25 @@ __global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* __re
     if (wid == 0) {
       unsigned long long w = s_w[lane];
       for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
         if (lane >= o) w += y;
       }
       s_w[lane] = w;
     }
     __syncthreads();
-    unsigned long long incl = x + (wid > 0 ? s_w[wid - 1] : 0ull) + s_carry;
-    if (i < n) part[i] = incl - v;
+    const unsigned long long incl = x + (wid > 0 ? s_w[wid - 1] : 0ull) + s_carry;
+    const unsigned long long start = incl - v;
+    if (i < T) {
+      const bool fits = incl <= (unsigned long long)cap;
+      ranges[i] = fits ? make_uint2((uint32_t)start, (uint32_t)incl) : make_uint2(0u, 0u);
+      counts[i] = fits ? (uint32_t)start : 0u;
+    }
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = incl;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    unsigned long long total = s_carry;
+    const unsigned long long total = s_carry;
     hdr->needed = total;
     if ((int64_t)total > cap) {
       hdr->status = SPLAT2D_ERR_CAPACITY;
@@ -89,104 +143,198 @@ __global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* __re
   }
 }
 
-struct BinArgs {
-  const uint32_t* ntiles;
-  const float4* records;
-  const unsigned long long* part;
-  const DView* views;
-  int32_t V;
-  int64_t R;
-  int64_t n_tiles;
-  int32_t tile_w, tile_h;
+// Stable LSD radix sort of `n` composite keys by their depth bits (high 32),
+// 8 bits per pass, ping-ponging between a and b (generic pointers: shared or
+// global memory), ranked per warp with match_any so that equal digits keep
+// their order.  4 passes: the result ends in `a`.  Needs NWARPS*256 counters.
+template <int NWARPS>
+__device__ void block_sort_depth(unsigned long long* a, unsigned long long* b, int n, uint32_t* cnt) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int per = (((n + NWARPS - 1) / NWARPS) + 31) & ~31;  // elements per warp, whole rounds
+  const int lo = min(wid * per, n), hi = min(lo + per, n);
+  for (int pass = 0; pass < 4; pass++) {
+    const int shift = 32 + 8 * pass;
+    unsigned long long* src = (pass & 1) ? b : a;
+    unsigned long long* dst = (pass & 1) ? a : b;
+    for (int i = threadIdx.x; i < NWARPS * 256; i += NWARPS * 32) cnt[i] = 0;
+    __syncthreads();
+    // per-warp digit counts
+    for (int base = lo; base < hi; base += 32) {
+      const int i = base + lane;
+      const uint32_t d = i < hi ? (uint32_t)(src[i] >> shift) & 0xffu : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      if (d < 256 && lane == __ffs(peers) - 1) cnt[wid * 256 + d] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    // exclusive offsets, digit-major then warp
+    if (threadIdx.x < 256) {
+      uint32_t acc = 0;
+      for (int w = 0; w < NWARPS; w++) {
+        const uint32_t c = cnt[w * 256 + threadIdx.x];
+        cnt[w * 256 + threadIdx.x] = acc;
+        acc += c;
+      }
+      cnt[NWARPS * 256 + threadIdx.x] = acc;  // digit total
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // exclusive scan of the 256 digit totals, 8 per lane
+      uint32_t v[8], s = 0;
+      for (int k = 0; k < 8; k++) {
+        v[k] = cnt[NWARPS * 256 + lane * 8 + k];
+        s += v[k];
+      }
+      uint32_t x = s;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      uint32_t run = x - s;
+      for (int k = 0; k < 8; k++) {
+        cnt[NWARPS * 256 + lane * 8 + k] = run;
+        run += v[k];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      const uint32_t dbase = cnt[NWARPS * 256 + threadIdx.x];
+      for (int w = 0; w < NWARPS; w++) cnt[w * 256 + threadIdx.x] += dbase;
+    }
+    __syncthreads();
+    // stable scatter
+    for (int base = lo; base < hi; base += 32) {
+      const int i = base + lane;
+      const unsigned long long key = i < hi ? src[i] : 0ull;
+      const uint32_t d = i < hi ? (uint32_t)(key >> shift) & 0xffu : 256u;
+      const uint32_t peers = __match_any_sync(0xffffffffu, d);
+      uint32_t pos = 0;
+      if (d < 256) pos = cnt[wid * 256 + d];
+      __syncwarp();
+      if (d < 256) {
+        if (lane == __ffs(peers) - 1) cnt[wid * 256 + d] = pos + __popc(peers);
+        dst[pos + __popc(peers & lt_mask)] = key;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  // equal depth bits: ascending surfel index (runs are short)
+  for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
+    const uint32_t d = (uint32_t)(a[i] >> 32);
+    const bool starts = (i == 0 || (uint32_t)(a[i - 1] >> 32) != d) && i + 1 < n && (uint32_t)(a[i + 1] >> 32) == d;
+    if (!starts) continue;
+    int e = i + 1;
+    while (e + 1 < n && (uint32_t)(a[e + 1] >> 32) == d) e++;
+    for (int x = i + 1; x <= e; x++) {
+      const unsigned long long key = a[x];
+      int y = x - 1;
+      while (y >= i && a[y] > key) {
+        a[y + 1] = a[y];
+        y--;
+      }
+      a[y + 1] = key;
+    }
+  }
+  __syncthreads();
+}
+
+constexpr int SEG_THREADS = 512;
+constexpr int SEG_WARPS = SEG_THREADS / 32;
+constexpr int SEG_SMEM_KEYS = 12288;  // keys per shared-memory bucket sort (two buffers)
+constexpr size_t SEG_SMEM_BYTES = 2 * sizeof(unsigned long long) * SEG_SMEM_KEYS + sizeof(uint32_t) * (SEG_WARPS + 1) * 256;
+
+struct SegArgs {
+  const uint2* ranges;
+  int64_t T;
+  unsigned long long* bucket;   // scattered composites (sorted in place for the large buckets)
+  unsigned long long* scratch;  // ping-pong space for the large buckets (same indexing as bucket)
+  uint64_t* keys;               // out: (tile << 32) | depth bits
+  uint32_t* vals;               // out: surfel index
   const Header* hdr;
-  uint64_t* keys;
-  uint32_t* vals;
+  uint32_t* queue;              // work counter
 };
 
-// Each thread owns 16 consecutive records of a 4096-record scan tile.
-__global__ void __launch_bounds__(256) k_bin(const BinArgs A) {
-  __shared__ unsigned long long s_w[8];
-  if (A.hdr->status != 0) return;  // overflow: emit nothing
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t b = blockIdx.x; b < A.n_tiles; b += gridDim.x) {
-    const int64_t r0 = b * SCAN_TILE + (int64_t)threadIdx.x * 16;
-    uint32_t cnt[16];
-    unsigned long long sum = 0;
-    if (r0 + 16 <= A.R) {
-      const uint4* p = reinterpret_cast<const uint4*>(A.ntiles + r0);
-#pragma unroll
-      for (int k = 0; k < 4; k++) {
-        uint4 q = __ldg(p + k);
-        cnt[4 * k] = q.x; cnt[4 * k + 1] = q.y; cnt[4 * k + 2] = q.z; cnt[4 * k + 3] = q.w;
-      }
+__global__ void __launch_bounds__(SEG_THREADS) k_tile_sort(const SegArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sa = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* sb = sa + SEG_SMEM_KEYS;
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(sb + SEG_SMEM_KEYS);
+  __shared__ int s_t;
+  if (A.hdr->status != 0) return;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = (int)atomicAdd(A.queue, 1u);
+    __syncthreads();
+    const int t = s_t;
+    __syncthreads();
+    if (t >= A.T) break;
+    const uint2 rg = A.ranges[t];
+    const int n = (int)(rg.y - rg.x);
+    if (n == 0) continue;
+    unsigned long long* src;
+    if (n <= SEG_SMEM_KEYS) {
+      for (int i = threadIdx.x; i < n; i += SEG_THREADS) sa[i] = A.bucket[rg.x + i];
+      __syncthreads();
+      block_sort_depth<SEG_WARPS>(sa, sb, n, cnt);
+      src = sa;
     } else {
-#pragma unroll
-      for (int k = 0; k < 16; k++) cnt[k] = (r0 + k < A.R) ? __ldg(A.ntiles + r0 + k) : 0u;
+      block_sort_depth<SEG_WARPS>(A.bucket + rg.x, A.scratch + rg.x, n, cnt);
+      src = A.bucket + rg.x;
     }
-#pragma unroll
-    for (int k = 0; k < 16; k++) sum += cnt[k];
-    // block exclusive scan of per-thread sums
-    unsigned long long x = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+    const uint64_t tile = (uint64_t)t << 32;
+    for (int i = threadIdx.x; i < n; i += SEG_THREADS) {
+      const unsigned long long key = src[i];
+      A.keys[rg.x + i] = tile | (key >> 32);
+      A.vals[rg.x + i] = (uint32_t)key;
     }
-    if (lane == 31) s_w[wid] = x;
     __syncthreads();
-    unsigned long long wpre = 0;
-    for (int w = 0; w < wid; w++) wpre += s_w[w];
-    unsigned long long off = A.part[b] + wpre + x - sum;
-    __syncthreads();
-    if (sum == 0) continue;
-    int v = find_view_by_record(A.views, A.V, r0);
-    for (int k = 0; k < 16; k++) {
-      const uint32_t n = cnt[k];
-      if (!n) continue;
-      const int64_t r = r0 + k;
-      while (v + 1 < A.V && A.views[v + 1].rbase <= r) v++;
-      const DView& vw = A.views[v];
-      const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
-      const uint32_t zb = __float_as_uint(f4.y);
-      const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
-      const int tx0 = (int)(q0 & 0xffffu) / A.tile_w, ty0 = (int)(q0 >> 16) / A.tile_h;
-      const int tx1 = (int)(q1 & 0xffffu) / A.tile_w, ty1 = (int)(q1 >> 16) / A.tile_h;
-      const uint32_t sidx = (uint32_t)(vw.soff + (r - vw.rbase));
-      for (int ty = ty0; ty <= ty1; ty++) {
-        for (int tx = tx0; tx <= tx1; tx++) {
-          const uint64_t tile = (uint64_t)(vw.tile_base + ty * vw.tiles_x + tx);
-          A.keys[off] = (tile << 32) | zb;
-          A.vals[off] = sidx;
-          off++;
-        }
-      }
-    }
   }
 }
 
-cudaError_t launch_bin(const Layout& L, const RastParams& P, char* ws, cudaStream_t st) {
-  if (L.R <= 0) return cudaSuccess;
-  const uint32_t* ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
-  unsigned long long* part = reinterpret_cast<unsigned long long*>(ws + L.scan_part);
+cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cudaStream_t st) {
+  if (L.R <= 0 || L.T <= 0) return cudaSuccess;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM_BYTES);
+    attr_set = true;
+  }
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
-  int grid = (int)min64(L.n_scan_tiles, (int64_t)sm_count() * 8);
-  k_scan_reduce<<<grid, 256, 0, st>>>(ntiles, L.R, part, L.n_scan_tiles);
-  count_launches(1);
-  k_scan_partials<<<1, 1024, 0, st>>>(part, L.n_scan_tiles, hdr, L.cap);
-  count_launches(1);
-  BinArgs A;
-  A.ntiles = ntiles;
+  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.tile_count);
+  uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)L.T, st);
+  if (e != cudaSuccess) return e;
+  TileBinArgs A;
+  A.ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
   A.records = reinterpret_cast<const float4*>(ws + L.records);
-  A.part = part;
   A.views = reinterpret_cast<const DView*>(ws + L.views);
   A.V = L.V;
   A.R = L.R;
-  A.n_tiles = L.n_scan_tiles;
   A.tile_w = P.tile_w;
   A.tile_h = P.tile_h;
+  A.counts = counts;
+  A.bucket = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   A.hdr = hdr;
-  A.keys = reinterpret_cast<uint64_t*>(ws + L.keys0);
-  A.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
-  k_bin<<<grid, 256, 0, st>>>(A);
+  const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 16);
+  k_tile_pass<false><<<grid, 256, 0, st>>>(A);
+  count_launches(1);
+  k_tile_scan<<<1, 1024, 0, st>>>(counts, ranges, L.T, hdr, L.cap);
+  count_launches(1);
+  k_tile_pass<true><<<grid, 256, 0, st>>>(A);
+  count_launches(1);
+  SegArgs S;
+  S.ranges = ranges;
+  S.T = L.T;
+  S.bucket = A.bucket;
+  S.scratch = reinterpret_cast<unsigned long long*>(ws + L.keys0);
+  S.keys = reinterpret_cast<uint64_t*>(ws + L.keys0);
+  S.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
+  S.hdr = hdr;
+  S.queue = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;
+  e = cudaMemsetAsync(S.queue, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const int sgrid = (int)min64(L.T, (int64_t)sm_count());
+  k_tile_sort<<<sgrid, SEG_THREADS, SEG_SMEM_BYTES, st>>>(S);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -356,20 +504,6 @@ cudaError_t launch_sort(uint64_t* keys0, uint32_t* vals0, uint64_t* keys1, uint3
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// tile ranges [start, end) in the sorted instance array
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ keys,
-                                                const unsigned long long* __restrict__ n_dev,
-                                                uint2* __restrict__ ranges) {
-  const int64_t n = (int64_t)*n_dev;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = (uint32_t)(keys[i] >> 32);
-    if (i == 0 || (uint32_t)(keys[i - 1] >> 32) != t) ranges[t].x = (uint32_t)i;
-    if (i == n - 1 || (uint32_t)(keys[i + 1] >> 32) != t) ranges[t].y = (uint32_t)(i + 1);
-  }
-}
-
 // Work order for the persistent render kernels: tiles bucketed by
 // floor(log2(list length)), longest first (a counting sort on the bucket).
 __global__ void __launch_bounds__(256) k_order_hist(const uint2* __restrict__ ranges, int64_t T,
@@ -410,18 +544,12 @@ __global__ void __launch_bounds__(256) k_order_scatter(const uint2* __restrict__
   }
 }
 
-cudaError_t launch_ranges(const Layout& L, const uint64_t* keys, char* ws, cudaStream_t st) {
-  uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
-  Header* hdr = reinterpret_cast<Header*>(ws + L.header);
-  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)L.T, st);
-  if (e != cudaSuccess) return e;
-  int grid = (int)min64((L.cap + 255) / 256, (int64_t)sm_count() * 8);
-  if (grid < 1) grid = 1;
-  k_ranges<<<grid, 256, 0, st>>>(keys, &hdr->n_inst, ranges);
-  count_launches(1);
+cudaError_t launch_order(const Layout& L, char* ws, cudaStream_t st) {
+  if (L.T <= 0) return cudaSuccess;
+  const uint2* ranges = reinterpret_cast<const uint2*>(ws + L.ranges);
   uint32_t* bins = reinterpret_cast<uint32_t*>(ws + L.tile_hist);
   uint32_t* order = reinterpret_cast<uint32_t*>(ws + L.tile_order);
-  e = cudaMemsetAsync(bins, 0, sizeof(uint32_t) * ORDER_BINS, st);
+  cudaError_t e = cudaMemsetAsync(bins, 0, sizeof(uint32_t) * ORDER_BINS, st);
   if (e != cudaSuccess) return e;
   int g2 = (int)min64((L.T + 255) / 256, (int64_t)sm_count() * 4);
   if (g2 < 1) g2 = 1;

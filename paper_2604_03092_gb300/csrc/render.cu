@@ -145,19 +145,89 @@ __device__ __forceinline__ uint32_t lane_word(const SRec* s_rec, int wd, int cou
   return cw & rw;
 }
 
+// Sum 8 per-lane values over the warp and give every lane all 8 totals
+// (a transposing butterfly: each level halves the values a lane keeps).
+__device__ __forceinline__ void warp_sum8_all(float (&v)[8], int lane) {
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const bool up = lane & 16;
+    const float send = up ? v[i] : v[i + 4];
+    const float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const bool up = lane & 8;
+    const float send = up ? v[i] : v[i + 2];
+    const float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  // lane L now holds the total of value index (L >> 2) & 7
+  const float t0 = v[0];
+#pragma unroll
+  for (int k = 0; k < 8; k++) v[k] = __shfl_sync(0xffffffffu, t0, k << 2);
+}
+
+// Warp-wide inclusive scans over lanes.
+__device__ __forceinline__ float warp_scan_mul(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = __fmul_rn(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_scan_add(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Per-pixel state of the forward while it is handed between warps.
+struct FwdState {
+  float T, C0, C1, C2, D, N0, N1, N2;
+  uint32_t last, done;
+};
+
+// Dynamic shared memory of the forward kernel.
+template <int NT, int CHUNK>
+struct FwdSmem {
+  SRec rec[CHUNK];
+  uint32_t bits[NT / 32][CHUNK / 32][32];
+  FwdState st[NT];
+  uint16_t list[NT / 32][CHUNK];
+  uint16_t apix[NT];
+  int item, nact, next;
+};
+
+// Tail mode of the forward: once at most this many pixels of a tile (per
+// warp) are still compositing, all warps share them, one pixel at a time.
+constexpr int kTailPerWarpFwd = 8;
+
 template <int TW, int TH, int CHUNK>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd(const RenderArgs A) {
-  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
-  __shared__ SRec s_rec[CHUNK];
-  __shared__ uint32_t s_bits[NW][NWD][32];
-  __shared__ int s_item;
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FwdSmem<NT, CHUNK>& S = *reinterpret_cast<FwdSmem<NT, CHUNK>*>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(&A.hdr->queue_fwd, 1u);
+    if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_fwd, 1u);
     __syncthreads();
-    const int item = s_item;
+    const int item = S.item;
     __syncthreads();
     if (item >= A.T) break;
     const int t = (int)__ldg(A.order + item);
@@ -174,44 +244,135 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
     uint32_t last = range.x;
     bool done = !inside;
     for (int64_t base = range.x; base < range.y; base += CHUNK) {
-      if (__syncthreads_count(!done) == 0) break;
+      const int n_act = __syncthreads_count(!done);
+      if (n_act == 0) break;
       const int count = (int)min64(CHUNK, (int64_t)range.y - base);
-      stage_chunk<NT, CHUNK>(A, vw, base, count, s_rec, nullptr);
+      if (threadIdx.x == 0) {
+        S.nact = 0;
+        S.next = 0;
+      }
+      stage_chunk<NT, CHUNK>(A, vw, base, count, S.rec, nullptr);
       __syncthreads();
-      if (__all_sync(0xffffffffu, done)) continue;
-      const int nwd = (count + 31) >> 5;
-      for (int wd = 0; wd < nwd; wd++) s_bits[wid][wd][lane] = lane_word(s_rec, wd, count, bx, by, lane);
-      // each lane walks its own pixel's entries, front to back
-      int wd = 0;
-      uint32_t b = done ? 0u : s_bits[wid][0][lane];
-      for (;;) {
-        while (b == 0 && !done && wd + 1 < nwd) b = s_bits[wid][++wd][lane];
-        const bool has = b != 0 && !done;
-        if (!__any_sync(0xffffffffu, has)) break;
-        if (!has) continue;
-        const int j = wd * 32 + __ffs(b) - 1;
-        b &= b - 1;
-        Pair e;
-        eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
-        n_eval++;
-        if (e.alpha < P.alpha_min) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-        if (Tn < P.t_min) {
-          done = true;
-          continue;
+      if (n_act > kTailPerWarpFwd * NW) {
+        // ---- bulk: each lane walks its own pixel's entries --------------------
+        if (__all_sync(0xffffffffu, done)) continue;
+        const int nwd = (count + 31) >> 5;
+        for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx, by, lane);
+        int wd = 0;
+        uint32_t b = done ? 0u : S.bits[wid][0][lane];
+        for (;;) {
+          while (b == 0 && !done && wd + 1 < nwd) b = S.bits[wid][++wd][lane];
+          const bool has = b != 0 && !done;
+          if (!__any_sync(0xffffffffu, has)) break;
+          if (!has) continue;
+          const int j = wd * 32 + __ffs(b) - 1;
+          b &= b - 1;
+          Pair e;
+          eval_pair(S.rec[j].c, S.rec[j].p, S.rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
+          n_eval++;
+          if (e.alpha < P.alpha_min) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
+          if (Tn < P.t_min) {
+            done = true;
+            continue;
+          }
+          const float w = __fmul_rn(e.alpha, T);
+          const float4 col = S.rec[j].col, nrm = S.rec[j].n;
+          C0 = __fmaf_rn(w, col.x, C0);
+          C1 = __fmaf_rn(w, col.y, C1);
+          C2 = __fmaf_rn(w, col.z, C2);
+          D = __fmaf_rn(w, col.w, D);
+          N0 = __fmaf_rn(w, nrm.x, N0);
+          N1 = __fmaf_rn(w, nrm.y, N1);
+          N2 = __fmaf_rn(w, nrm.z, N2);
+          T = Tn;
+          last = (uint32_t)(base + j + 1);
+          n_blend++;
         }
-        const float w = __fmul_rn(e.alpha, T);
-        const float4 col = s_rec[j].col, nrm = s_rec[j].n;
-        C0 = __fmaf_rn(w, col.x, C0);
-        C1 = __fmaf_rn(w, col.y, C1);
-        C2 = __fmaf_rn(w, col.z, C2);
-        D = __fmaf_rn(w, col.w, D);
-        N0 = __fmaf_rn(w, nrm.x, N0);
-        N1 = __fmaf_rn(w, nrm.y, N1);
-        N2 = __fmaf_rn(w, nrm.z, N2);
-        T = Tn;
-        last = (uint32_t)(base + j + 1);
-        n_blend++;
+      } else {
+        // ---- tail: warps pull the remaining pixels; a warp composites 32 of
+        //      a pixel's entries per step with a prefix product of (1 - alpha)
+        if (!done) {
+          const int k = atomicAdd(&S.nact, 1);
+          S.apix[k] = (uint16_t)threadIdx.x;
+          S.st[threadIdx.x] = FwdState{T, C0, C1, C2, D, N0, N1, N2, last, 0u};
+        }
+        __syncthreads();
+        for (;;) {
+          int k = 0;
+          if (lane == 0) k = atomicAdd(&S.next, 1);
+          k = __shfl_sync(0xffffffffu, k, 0);
+          if (k >= n_act) break;
+          const int pth = S.apix[k];
+          const int pw = pth >> 5, pl = pth & 31;
+          const int qx = tx0 + (pw % WX) * 8 + (pl & 7), qy = ty0 + (pw / WX) * 4 + (pl >> 3);
+          const float fx = (float)qx + 0.5f, fy = (float)qy + 0.5f;
+          FwdState st = S.st[pth];
+          float acc[8] = {st.C0, st.C1, st.C2, st.D, st.N0, st.N1, st.N2, 0.f};
+          float tt = st.T;
+          uint32_t lst = st.last;
+          bool dn = false;
+          // this pixel's entries of the chunk, ascending
+          int nrel = 0;
+          for (int wd = 0; wd < (count + 31) >> 5; wd++) {
+            const int j = wd * 32 + lane;
+            const bool rel = j < count && in_rect(S.rec[j].rect, qx, qy);
+            const uint32_t bb = __ballot_sync(0xffffffffu, rel);
+            if (rel) S.list[wid][nrel + __popc(bb & lt_mask)] = (uint16_t)j;
+            nrel += __popc(bb);
+          }
+          __syncwarp();
+          for (int g = 0; g < nrel && !dn; g += 32) {
+            const bool has = g + lane < nrel;
+            const int j = has ? (int)S.list[wid][g + lane] : 0;
+            Pair e;
+            float alpha = 0.f;
+            if (has) {
+              eval_pair(S.rec[j].c, S.rec[j].p, S.rec[j].q, fx, fy, P.lp_scale, P.alpha_max, e);
+              alpha = e.alpha;
+            }
+            const bool kept = has && alpha >= P.alpha_min;
+            const float f = kept ? __fsub_rn(1.f, alpha) : 1.f;
+            const float Pin = warp_scan_mul(f, lane);
+            float Pex = __shfl_up_sync(0xffffffffu, Pin, 1);
+            if (lane == 0) Pex = 1.f;
+            const float Tb = __fmul_rn(tt, Pex), Ta = __fmul_rn(tt, Pin);
+            const uint32_t stopb = __ballot_sync(0xffffffffu, kept && Ta < P.t_min);
+            const int sl = stopb ? __ffs(stopb) - 1 : 32;
+            const bool contrib = kept && lane < sl;
+            const float w = contrib ? __fmul_rn(alpha, Tb) : 0.f;
+            float vals[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (contrib) {
+              const float4 col = S.rec[j].col, nrm = S.rec[j].n;
+              vals[0] = w * col.x; vals[1] = w * col.y; vals[2] = w * col.z; vals[3] = w * col.w;
+              vals[4] = w * nrm.x; vals[5] = w * nrm.y; vals[6] = w * nrm.z;
+            }
+            warp_sum8_all(vals, lane);
+#pragma unroll
+            for (int q = 0; q < 7; q++) acc[q] += vals[q];
+            n_eval += (has && lane <= sl) ? 1u : 0u;
+            n_blend += contrib ? 1u : 0u;
+            const uint32_t cb = __ballot_sync(0xffffffffu, contrib);
+            if (cb) lst = (uint32_t)(base + __shfl_sync(0xffffffffu, j, 31 - __clz(cb)) + 1);
+            if (stopb) {
+              tt = __shfl_sync(0xffffffffu, Tb, sl);
+              dn = true;
+            } else {
+              tt = __shfl_sync(0xffffffffu, Ta, 31);
+            }
+          }
+          if (lane == 0)
+            S.st[pth] = FwdState{tt, acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6], lst, dn ? 1u : 0u};
+          __syncwarp();
+        }
+        __syncthreads();
+        if (!done) {
+          const FwdState st = S.st[threadIdx.x];
+          T = st.T; C0 = st.C0; C1 = st.C1; C2 = st.C2; D = st.D;
+          N0 = st.N0; N1 = st.N1; N2 = st.N2;
+          last = st.last;
+          done = st.done != 0u;
+        }
       }
     }
     if (inside) {
@@ -289,124 +450,181 @@ __device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const
   }
 }
 
+// Dynamic shared memory of the backward kernel.
+template <int NT, int CHUNK>
+struct BwdSmem {
+  SRec rec[CHUNK];
+  float grad[CHUNK * SGRAD_STRIDE];
+  uint32_t idx[CHUNK];
+  uint16_t list[NT / 32][CHUNK];
+  float2 tq[NT];       // (T, Q) of each pixel between chunks
+  uint16_t apix[NT];
+  int item, nact, next;
+  uint32_t top;
+};
+
+// The reverse pass is entry-parallel throughout: per chunk, the tile's pixels
+// that still have entries in it are pulled by the warps one at a time; a warp
+// takes 32 of the pixel's entries per step (lane 0 the deepest), recovers the
+// transmittance in front of each by a prefix product of 1/(1 - alpha) and the
+// suffix sum behind each by a prefix sum, and every lane adds its own entry's
+// gradient to that entry's shared-memory slot.
 template <int TW, int TH, int CHUNK>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(const RenderArgs A) {
-  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
-  __shared__ SRec s_rec[CHUNK];
-  __shared__ uint32_t s_idx[CHUNK];
-  __shared__ float s_grad[CHUNK * SGRAD_STRIDE];
-  __shared__ uint32_t s_bits[NW][NWD][32];
-  __shared__ int s_item;
-  __shared__ uint32_t s_top;
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BwdSmem<NT, CHUNK>& S = *reinterpret_cast<BwdSmem<NT, CHUNK>*>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
-  for (int i = threadIdx.x; i < CHUNK * SGRAD_STRIDE; i += NT) s_grad[i] = 0.f;
+  for (int i = threadIdx.x; i < CHUNK * SGRAD_STRIDE; i += NT) S.grad[i] = 0.f;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(&A.hdr->queue_bwd, 1u);
+    if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_bwd, 1u);
     __syncthreads();
-    const int item = s_item;
+    const int item = S.item;
     if (item >= A.T) break;
     const int t = (int)__ldg(A.order + item);
     const int v = find_view_by_tile(A.views, A.V, t);
     const DView& vw = A.views[v];
     const int lt = t - vw.tile_base;
     const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
-    const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
-    const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
+    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7);
+    const int ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
     const bool inside = ipx < vw.W && ipy < vw.H;
-    const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
     const int64_t HW = (int64_t)vw.W * vw.H;
-    const int64_t pix = (int64_t)ipy * vw.W + ipx;
     uint32_t my_last = range.x;
-    float T = 1.f, dC0 = 0.f, dC1 = 0.f, dC2 = 0.f, dD = 0.f, dN0 = 0.f, dN1 = 0.f, dN2 = 0.f, dA = 0.f;
+    float T = 1.f, Q = 0.f;
     if (inside) {
+      const int64_t pix = (int64_t)ipy * vw.W + ipx;
       my_last = A.last[vw.poff + pix];
       T = A.tfinal[vw.poff + pix];
       if (A.d_rgb) {
         const float* g = A.d_rgb + 3 * vw.poff + pix;
-        dC0 = g[0]; dC1 = g[HW]; dC2 = g[2 * HW];
+        Q = T * (g[0] * P.bg[0] + g[HW] * P.bg[1] + g[2 * HW] * P.bg[2]);
       }
-      if (A.d_depth) dD = A.d_depth[vw.poff + pix];
-      if (A.d_normal) {
-        const float* g = A.d_normal + 3 * vw.poff + pix;
-        dN0 = g[0]; dN1 = g[HW]; dN2 = g[2 * HW];
-      }
-      if (A.d_alpha) dA = A.d_alpha[vw.poff + pix];
     }
-    const float T_final = T;
-    float Q = T_final * (dC0 * P.bg[0] + dC1 * P.bg[1] + dC2 * P.bg[2]);
-    const float dAT = dA * T_final;
-    if (threadIdx.x == 0) s_top = range.x;
+    if (threadIdx.x == 0) S.top = range.x;
     __syncthreads();
-    if (my_last > range.x) atomicMax(&s_top, my_last);
+    if (my_last > range.x) atomicMax(&S.top, my_last);
     __syncthreads();
-    const uint32_t top = s_top;
+    const uint32_t top = S.top;
     for (int64_t hi = top; hi > (int64_t)range.x; hi -= CHUNK) {
       const int64_t lo = max64((int64_t)range.x, hi - CHUNK);
       const int count = (int)(hi - lo);
-      stage_chunk<NT, CHUNK>(A, vw, lo, count, s_rec, s_idx);
+      const bool act = (int64_t)my_last > lo;
+      if (threadIdx.x == 0) {
+        S.nact = 0;
+        S.next = 0;
+      }
+      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx);
       __syncthreads();
-      const int lim = (int)min64((int64_t)my_last - lo, count);  // entries below this pixel's last
-      if (__any_sync(0xffffffffu, lim > 0)) {
-        const int nwd = (count + 31) >> 5;
-        for (int wd = 0; wd < nwd; wd++) {
-          uint32_t m = lane_word(s_rec, wd, count, bx, by, lane);
-          const int keep = lim - wd * 32;
-          m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
-          s_bits[wid][wd][lane] = m;
-        }
-        // each lane walks its own pixel's entries, back to front
-        int wd = nwd - 1;
-        uint32_t b = s_bits[wid][wd][lane];
-        for (;;) {
-          while (b == 0 && wd > 0) b = s_bits[wid][--wd][lane];
-          const bool has = b != 0;
-          if (!__any_sync(0xffffffffu, has)) break;
-          if (!has) continue;
-          const int jj = 31 - __clz(b);
-          b &= ~(1u << jj);
-          const int j = wd * 32 + jj;
-          Pair e;
-          eval_pair(s_rec[j].c, s_rec[j].p, s_rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
-          n_eval++;
-          if (e.alpha < P.alpha_min) continue;
-          n_blend++;
-          const float4 col = s_rec[j].col, nrm = s_rec[j].n;
-          const float iom = rcp_approx(__fsub_rn(1.f, e.alpha));
-          const float Ti = T * iom;
-          const float w = e.alpha * Ti;
-          const float f = fmaf(dC0, col.x, fmaf(dC1, col.y, fmaf(dC2, col.z, fmaf(dD, col.w,
-                          fmaf(dN0, nrm.x, fmaf(dN1, nrm.y, dN2 * nrm.z))))));
-          const float da = Ti * f - (Q - dAT) * iom;
-          Q = fmaf(w, f, Q);
-          T = Ti;
-          float g[16];
-          float gz;
-          pair_grads(e, s_rec[j].p, s_rec[j].q, da, w, dC0, dC1, dC2, dD, dN0, dN1, dN2, P.lp_scale, g, gz);
-          float* sg = s_grad + j * SGRAD_STRIDE;
-#pragma unroll
-          for (int k = 0; k < 16; k++) atomicAdd(sg + k, g[k]);
-          atomicAdd(sg + 16, gz);
-        }
+      if (act) {
+        const int k = atomicAdd(&S.nact, 1);
+        S.apix[k] = (uint16_t)threadIdx.x;
+        S.tq[threadIdx.x] = make_float2(T, Q);
       }
       __syncthreads();
+      const int n_act = S.nact;
+      for (;;) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(&S.next, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= n_act) break;
+        const int pth = S.apix[k];
+        const int pw = pth >> 5, pl = pth & 31;
+        const int qx = tx0 + (pw % WX) * 8 + (pl & 7), qy = ty0 + (pw / WX) * 4 + (pl >> 3);
+        const float fx = (float)qx + 0.5f, fy = (float)qy + 0.5f;
+        const int64_t qpix = vw.poff + (int64_t)qy * vw.W + qx;
+        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f, e5 = 0.f, e6 = 0.f, eA = 0.f;
+        if (A.d_rgb) {
+          const float* g = A.d_rgb + 3 * vw.poff + (int64_t)qy * vw.W + qx;
+          e0 = __ldg(g); e1 = __ldg(g + HW); e2 = __ldg(g + 2 * HW);
+        }
+        if (A.d_depth) e3 = __ldg(A.d_depth + qpix);
+        if (A.d_normal) {
+          const float* g = A.d_normal + 3 * vw.poff + (int64_t)qy * vw.W + qx;
+          e4 = __ldg(g); e5 = __ldg(g + HW); e6 = __ldg(g + 2 * HW);
+        }
+        if (A.d_alpha) eA = __ldg(A.d_alpha + qpix);
+        const float eAT = eA * A.tfinal[qpix];
+        const int jmax = (int)min64((int64_t)A.last[qpix] - lo, count);
+        float2 tq = S.tq[pth];
+        float tt = tq.x, qq_ = tq.y;
+        // this pixel's entries of the chunk below its last, ascending
+        int nrel = 0;
+        for (int wd = 0; wd < (jmax + 31) >> 5; wd++) {
+          const int j = wd * 32 + lane;
+          const bool rel = j < jmax && in_rect(S.rec[j].rect, qx, qy);
+          const uint32_t bb = __ballot_sync(0xffffffffu, rel);
+          if (rel) S.list[wid][nrel + __popc(bb & lt_mask)] = (uint16_t)j;
+          nrel += __popc(bb);
+        }
+        __syncwarp();
+        for (int gend = nrel; gend > 0; gend -= 32) {
+          const int idx = gend - 1 - lane;  // lane 0 = the deepest entry of this step
+          const bool has = idx >= 0;
+          const int j = has ? (int)S.list[wid][idx] : 0;
+          Pair e;
+          float alpha = 0.f;
+          if (has) {
+            eval_pair(S.rec[j].c, S.rec[j].p, S.rec[j].q, fx, fy, P.lp_scale, P.alpha_max, e);
+            alpha = e.alpha;
+          }
+          const bool kept = has && alpha >= P.alpha_min;
+          const float iom = kept ? rcp_approx(__fsub_rn(1.f, alpha)) : 1.f;
+          const float Tb = tt * warp_scan_mul(iom, lane);  // transmittance in front of this entry
+          const float w = kept ? alpha * Tb : 0.f;
+          float f = 0.f;
+          if (kept) {
+            const float4 col = S.rec[j].col, nrm = S.rec[j].n;
+            f = fmaf(e0, col.x, fmaf(e1, col.y, fmaf(e2, col.z, fmaf(e3, col.w,
+                fmaf(e4, nrm.x, fmaf(e5, nrm.y, e6 * nrm.z))))));
+          }
+          const float wf = w * f;
+          const float Sin = warp_scan_add(wf, lane);
+          const float Qb = qq_ + (Sin - wf);  // sum over the entries behind this one
+          n_eval += has ? 1u : 0u;
+          if (kept) {
+            n_blend++;
+            const float da = Tb * f - (Qb - eAT) * iom;
+            float g[16];
+            float gz;
+            pair_grads(e, S.rec[j].p, S.rec[j].q, da, w, e0, e1, e2, e3, e4, e5, e6, P.lp_scale, g, gz);
+            float* sg = S.grad + j * SGRAD_STRIDE;
+#pragma unroll
+            for (int q = 0; q < 16; q++)
+              if (g[q] != 0.f) atomicAdd(sg + q, g[q]);
+            if (gz != 0.f) atomicAdd(sg + 16, gz);
+          }
+          tt = __shfl_sync(0xffffffffu, Tb, min(31, gend - 1));
+          qq_ += __shfl_sync(0xffffffffu, Sin, 31);
+        }
+        if (lane == 0) S.tq[pth] = make_float2(tt, qq_);
+        __syncwarp();
+      }
+      __syncthreads();
+      if (act) {
+        const float2 tq = S.tq[threadIdx.x];
+        T = tq.x;
+        Q = tq.y;
+      }
       // flush this chunk's per-entry sums: one set of vector atomics per entry
       for (int j = threadIdx.x; j < count; j += NT) {
-        float* sg = s_grad + j * SGRAD_STRIDE;
+        float* sg = S.grad + j * SGRAD_STRIDE;
         float acc = 0.f;
 #pragma unroll
-        for (int k = 0; k < 17; k++) acc += fabsf(sg[k]);
+        for (int q = 0; q < 17; q++) acc += fabsf(sg[q]);
         if (acc != 0.f) {
-          float* dst = A.rgrad + (int64_t)s_idx[j] * GRAD_F;
+          float* dst = A.rgrad + (int64_t)S.idx[j] * GRAD_F;
           red_add_v4(dst + 0, sg[0], sg[1], sg[2], sg[3]);
           red_add_v4(dst + 4, sg[4], sg[5], sg[6], sg[7]);
           red_add_v4(dst + 8, sg[8], sg[9], sg[10], sg[11]);
           red_add_v4(dst + 12, sg[12], sg[13], sg[14], sg[15]);
           atomicAdd(dst + 16, sg[16]);
 #pragma unroll
-          for (int k = 0; k < 17; k++) sg[k] = 0.f;
+          for (int q = 0; q < 17; q++) sg[q] = 0.f;
         }
       }
       __syncthreads();
@@ -448,9 +666,9 @@ static RenderArgs make_args(const Layout& L, const RastParams& P, char* ws, cons
 }
 
 template <typename K>
-static int persistent_grid(K kernel, int threads, int64_t work) {
+static int persistent_grid(K kernel, int threads, size_t smem, int64_t work) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (per_sm < 1) per_sm = 1;
   int64_t g = (int64_t)per_sm * sm_count();
   if (g > work) g = work;
@@ -460,26 +678,30 @@ static int persistent_grid(K kernel, int threads, int64_t work) {
 template <int TW, int TH, int CHUNK>
 static cudaError_t run_fwd(const RenderArgs& A, cudaStream_t st) {
   auto k = k_render_fwd<TW, TH, CHUNK>;
+  constexpr size_t smem = sizeof(FwdSmem<TW * TH, CHUNK>);
   static int grid = -1;
   static int64_t grid_T = -1;
+  if (grid < 0) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (grid < 0 || grid_T != A.T) {
-    grid = persistent_grid(k, TW * TH, A.T);
+    grid = persistent_grid(k, TW * TH, smem, A.T);
     grid_T = A.T;
   }
-  k<<<grid, TW * TH, 0, st>>>(A);
+  k<<<grid, TW * TH, smem, st>>>(A);
   count_launches(1);
   return cudaGetLastError();
 }
 template <int TW, int TH, int CHUNK>
 static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
   auto k = k_render_bwd<TW, TH, CHUNK>;
+  constexpr size_t smem = sizeof(BwdSmem<TW * TH, CHUNK>);
   static int grid = -1;
   static int64_t grid_T = -1;
+  if (grid < 0) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (grid < 0 || grid_T != A.T) {
-    grid = persistent_grid(k, TW * TH, A.T);
+    grid = persistent_grid(k, TW * TH, smem, A.T);
     grid_T = A.T;
   }
-  k<<<grid, TW * TH, 0, st>>>(A);
+  k<<<grid, TW * TH, smem, st>>>(A);
   count_launches(1);
   return cudaGetLastError();
 }

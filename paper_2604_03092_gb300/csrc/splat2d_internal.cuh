@@ -87,18 +87,16 @@ constexpr float kLn2 = 0.69314718055994531f;
 // Workspace layout (identical on every call for the same problem)
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t header, views, groups, ntiles, records, rgrad, scan_part, keys0, keys1, vals0, vals1, sort_hist,
-      ranges, tile_order, tile_hist, tfinal, last, total;
+  size_t header, views, groups, ntiles, records, rgrad, keys0, keys1, vals0, vals1, sort_hist, ranges,
+      tile_count, tile_order, tile_hist, tfinal, last, total;
   int64_t R, T, P, cap;
   int64_t n_work;     // sum over view groups of the surfel range sizes
   int32_t V, G;
   bool groups_overlap;  // some surfel belongs to two groups
-  int64_t n_scan_tiles;
   int32_t sort_blocks;
   int32_t key_bits;
 };
 
-constexpr int SCAN_TILE = 4096;   // records per scan block
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_IPT = 8;
 constexpr int SORT_TILE = SORT_THREADS * SORT_IPT;  // 2048 keys per tile
@@ -128,11 +126,11 @@ struct RastParams {
 cudaError_t launch_upload(const void* host_src, size_t bytes, void* dst, cudaStream_t st);
 cudaError_t launch_preprocess(const splat2d_surfels* S, const Layout& L, const RastParams& P, char* ws,
                               cudaStream_t st);
-cudaError_t launch_bin(const Layout& L, const RastParams& P, char* ws, cudaStream_t st);
+cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cudaStream_t st);
+cudaError_t launch_order(const Layout& L, char* ws, cudaStream_t st);
 cudaError_t launch_sort(uint64_t* keys0, uint32_t* vals0, uint64_t* keys1, uint32_t* vals1,
                         const unsigned long long* n_dev, int64_t n_max, int key_bits, uint32_t* hist,
                         int sort_blocks, int* final_buffer, cudaStream_t st);
-cudaError_t launch_ranges(const Layout& L, const uint64_t* keys, char* ws, cudaStream_t st);
 cudaError_t launch_render_fwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
                               float* rgb, float* depth, float* normal, float* alpha, cudaStream_t st);
 cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
