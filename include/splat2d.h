@@ -254,6 +254,22 @@ size_t splat2d_sort_tmp_size(int64_t n);
 int splat2d_sort_pairs(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits, void* tmp, size_t tmp_bytes,
                        splat2d_stream stream);
 
+/*
+ * splat2d_sort_pairs without any allocation: the same stable sort, with its
+ * scratch in a fixed device array inside the library instead of a caller
+ * buffer.  The paper has no counterpart; this serves callers that cannot
+ * allocate device memory (code running during CUDA-graph capture, real-time
+ * loops with a no-allocation rule, plug-ins whose host application owns all
+ * device memory).  n must not exceed SPLAT2D_SORT_NOALLOC_MAX_PAIRS
+ * (SPLAT2D_ERR_INVALID_ARG otherwise).  The array (about 13 MB) is held on
+ * every GPU that loads the library until the process exits.  All calls share
+ * it, so calls that overlap on the GPU race; calls on one stream are safe.
+ * The first call on a device looks up the array's address with that device
+ * current: make it before any stream capture.
+ */
+#define SPLAT2D_SORT_NOALLOC_MAX_PAIRS (1 << 20)
+int splat2d_sort_pairs_noalloc(uint64_t* keys, uint32_t* vals, int64_t n, int key_bits, splat2d_stream stream);
+
 /* Human-readable name of a status code. */
 const char* splat2d_strerror(int code);
 

@@ -18,6 +18,7 @@ ERR_CAPACITY = -4
 ERR_TIMEOUT = -5
 ERR_NO_DEVICE = -6
 FLAG_NO_STATS = 1
+SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 
 class View(ctypes.Structure):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "splat2d_sort_tmp_size": (c_size_t, [c_int64]),
     "splat2d_sort_pairs": (ctypes.c_int, [c_void_p, c_void_p, c_int64, ctypes.c_int, c_void_p, c_size_t,
                                           c_void_p]),
+    "splat2d_sort_pairs_noalloc": (ctypes.c_int, [c_void_p, c_void_p, c_int64, ctypes.c_int, c_void_p]),
     "splat2d_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
