@@ -210,6 +210,7 @@ def main():
     ap.add_argument("--workload", default="submap32")
     ap.add_argument("--tile", default=None, help="WxH, e.g. 16x16 (default: autotune cache or 16x16)")
     ap.add_argument("--chunk", type=int, default=None)
+    ap.add_argument("--fwd-tail", type=int, default=None, help="forward tail threshold per warp (255 = always)")
     ap.add_argument("--plain-steps", type=int, default=2, help="steps of the per-view plain-launch baseline (0=skip)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-pixels", type=int, default=8192, help="pixels of the oracle CPU-baseline sample")
@@ -254,6 +255,8 @@ def main():
         cfg.tile_w, cfg.tile_h = (int(x) for x in args.tile.lower().split("x"))
     if args.chunk:
         cfg.chunk = args.chunk
+    if args.fwd_tail is not None:
+        cfg.fwd_tail = args.fwd_tail
     rast = Rasterizer(sc.views, sc.n, cfg, device=dev)
     im = rast.forward(*params)  # sizes the instance capacity (synchronises once)
     st0 = rast.stats()
@@ -473,7 +476,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ray-cast indoor submap; stands in for ScanNet/BundleFusion)",
             "config": {"workload": args.workload, "description": wl_desc, "views": V, "surfels": sc.n,
-                       "tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk, "instances": n_inst,
+                       "tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk, "fwd_tail": cfg.fwd_tail, "instances": n_inst,
                        "visible_pairs": n_vis, "l2": "inputs larger than L2 (records + instances > 129 MB)",
                        "parallelism": f"{world} independent submap(s), one per GPU"},
             "stages_ms": stage_ms, "stage_roofline": stage_frac,

@@ -107,7 +107,7 @@ typedef struct {
  * z_near 0.01, black background. */
 typedef struct {
   int32_t tile_w, tile_h;   /* one of 8x8, 16x16, 32x8 */
-  int32_t chunk;            /* surfels staged per shared-memory batch: 64, 128 or 256 */
+  int32_t chunk;            /* surfels staged per shared-memory batch: 64, 128, 256 (or 512 with 256-pixel tiles) */
   float alpha_min;          /* skip pairs with alpha below this */
   float alpha_max;          /* clamp of alpha (keeps the reverse pass finite) */
   float t_min;              /* stop a pixel before T would drop below this */
@@ -119,6 +119,11 @@ typedef struct {
 
 /* flags */
 #define SPLAT2D_FLAG_NO_STATS 1u   /* skip the pair counters (kept by default) */
+/* Bits 8..15 of flags: forward tail threshold, pixels per warp of a tile below
+ * which the forward shares the tile's remaining pixels across all warps
+ * (0 = the default of 8; 255 = always).  A launch-shape knob for the
+ * autotuner: it changes the schedule, not the result beyond rounding. */
+#define SPLAT2D_FLAG_TAIL_SHIFT 8
 
 /* The shape of one problem: the views (host array) and sizes.  Pass the same
  * problem (same values) to every call that uses one workspace. */

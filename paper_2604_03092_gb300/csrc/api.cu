@@ -37,7 +37,8 @@ static bool valid_config(const splat2d_config* c) {
   if (!c) return false;
   const bool tile_ok = (c->tile_w == 16 && c->tile_h == 16) || (c->tile_w == 8 && c->tile_h == 8) ||
                        (c->tile_w == 32 && c->tile_h == 8);
-  const bool chunk_ok = c->chunk == 64 || c->chunk == 128 || c->chunk == 256;
+  const bool chunk_ok = c->chunk == 64 || c->chunk == 128 || c->chunk == 256 ||
+                        (c->chunk == 512 && c->tile_w * c->tile_h == 256);
   if (!tile_ok || !chunk_ok) return false;
   if (!(c->alpha_min > 0.f && c->alpha_min < 1.f)) return false;
   if (!(c->alpha_max >= c->alpha_min && c->alpha_max < 1.f)) return false;
@@ -182,6 +183,8 @@ static RastParams make_params(const splat2d_config* c) {
   P.tile_w = c->tile_w;
   P.tile_h = c->tile_h;
   P.stats = (c->flags & SPLAT2D_FLAG_NO_STATS) ? 0 : 1;
+  const int tail = (int)((c->flags >> SPLAT2D_FLAG_TAIL_SHIFT) & 0xffu);
+  P.fwd_tail = tail == 0 ? 8 : (tail == 255 ? 1 << 20 : tail);
   return P;
 }
 

@@ -25,28 +25,32 @@
 
 namespace s2d {
 
-// Shared-memory copy of a render record (unpacked), 96 bytes.
-struct SRec {
-  float4 c;   // cx_hi, cy_hi, cx_lo, cy_lo
-  float4 p;   // p00 p01 p10 p11
-  float4 q;   // p20 p21 p22 opacity
-  float4 col; // r g b z
-  float4 n;   // nx ny nz -
-  int4 rect;  // x0 y0 (x1 - x0) (y1 - y0)
+// Shared-memory copy of a chunk of render records, unpacked, stored field by
+// field (structure of arrays) so that lanes reading different records hit
+// consecutive 16-byte slots instead of colliding banks.
+template <int CHUNK>
+struct SRecs {
+  float4 c[CHUNK];    // cx_hi, cy_hi, cx_lo, cy_lo
+  float4 p[CHUNK];    // p00 p01 p10 p11
+  float4 q[CHUNK];    // p20 p21 p22 opacity
+  float4 col[CHUNK];  // r g b z
+  float4 n[CHUNK];    // nx ny nz -
+  int4 rect[CHUNK];   // x0 y0 (x1 - x0) (y1 - y0)
 };
 
-__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRec& o) {
+template <int CHUNK>
+__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRecs<CHUNK>& o, int j) {
   const float4 f0 = __ldg(rec + 0), f1 = __ldg(rec + 1), f2 = __ldg(rec + 2), f3 = __ldg(rec + 3),
                f4 = __ldg(rec + 4);
   const float2 lo = unpack_half2_scaled(__float_as_uint(f0.z));
-  o.c = make_float4(f0.x, f0.y, lo.x, lo.y);
-  o.p = f1;
-  o.q = make_float4(f2.x, f2.y, f2.z, f0.w);
-  o.col = make_float4(f2.w, f3.x, f3.y, f4.y);
-  o.n = make_float4(f3.z, f3.w, f4.x, 0.f);
+  o.c[j] = make_float4(f0.x, f0.y, lo.x, lo.y);
+  o.p[j] = f1;
+  o.q[j] = make_float4(f2.x, f2.y, f2.z, f0.w);
+  o.col[j] = make_float4(f2.w, f3.x, f3.y, f4.y);
+  o.n[j] = make_float4(f3.z, f3.w, f4.x, 0.f);
   const uint32_t r0 = __float_as_uint(f4.z), r1 = __float_as_uint(f4.w);
   const int x0 = (int)(r0 & 0xffffu), y0 = (int)(r0 >> 16), x1 = (int)(r1 & 0xffffu), y1 = (int)(r1 >> 16);
-  o.rect = make_int4(x0, y0, x1 - x0, y1 - y0);
+  o.rect[j] = make_int4(x0, y0, x1 - x0, y1 - y0);
 }
 
 // alpha of one (pixel, record) pair.  Written with explicit round-to-nearest
@@ -104,11 +108,11 @@ struct RenderArgs {
 // Stage entries [base, base + count) of the sorted list into shared memory.
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                            SRec* s_rec, uint32_t* s_idx) {
+                                            SRecs<CHUNK>& s_rec, uint32_t* s_idx) {
   for (int j = threadIdx.x; j < count; j += NT) {
     const uint32_t s = __ldg(A.vals + base + j);
     const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
-    unpack_record(A.records + rec * REC_F4, s_rec[j]);
+    unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j);
     if (s_idx) s_idx[j] = (uint32_t)rec;
   }
 }
@@ -118,11 +122,12 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
 // returns the bits of the entries whose pixel rect holds this lane's pixel:
 // the warp ballots, per patch column and per patch row, which entries'
 // rects span it, and each lane ANDs its column's and its row's ballot.
-__device__ __forceinline__ uint32_t lane_word(const SRec* s_rec, int wd, int count, int bx, int by, int lane) {
+template <int CHUNK>
+__device__ __forceinline__ uint32_t lane_word(const SRecs<CHUNK>& s_rec, int wd, int count, int bx, int by, int lane) {
   const int j = wd * 32 + lane;
   uint32_t cm = 0, rm = 0;
   if (j < count) {
-    const int4 r = s_rec[j].rect;  // x0, y0, x1 - x0, y1 - y0
+    const int4 r = s_rec.rect[j];  // x0, y0, x1 - x0, y1 - y0
     const int c0 = max(r.x - bx, 0), c1 = min(r.x + r.z - bx, 7);
     const int r0 = max(r.y - by, 0), r1 = min(r.y + r.w - by, 3);
     if (c0 <= c1 && r0 <= r1) {
@@ -203,7 +208,7 @@ struct FwdState {
 // Dynamic shared memory of the forward kernel.
 template <int NT, int CHUNK>
 struct FwdSmem {
-  SRec rec[CHUNK];
+  SRecs<CHUNK> rec;
   uint32_t bits[NT / 32][CHUNK / 32][32];
   FwdState st[NT];
   uint16_t list[NT / 32][CHUNK];
@@ -211,9 +216,8 @@ struct FwdSmem {
   int item, nact, next;
 };
 
-// Tail mode of the forward: once at most this many pixels of a tile (per
-// warp) are still compositing, all warps share them, one pixel at a time.
-constexpr int kTailPerWarpFwd = 8;
+// Tail mode of the forward: once at most P.fwd_tail pixels of a tile per
+// warp are still compositing, all warps share them, one pixel at a time.
 
 template <int TW, int TH, int CHUNK>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd(const RenderArgs A) {
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
       }
       stage_chunk<NT, CHUNK>(A, vw, base, count, S.rec, nullptr);
       __syncthreads();
-      if (n_act > kTailPerWarpFwd * NW) {
+      if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
         if (__all_sync(0xffffffffu, done)) continue;
         const int nwd = (count + 31) >> 5;
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
           const int j = wd * 32 + __ffs(b) - 1;
           b &= b - 1;
           Pair e;
-          eval_pair(S.rec[j].c, S.rec[j].p, S.rec[j].q, px, py, P.lp_scale, P.alpha_max, e);
+          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], px, py, P.lp_scale, P.alpha_max, e);
           n_eval++;
           if (e.alpha < P.alpha_min) continue;
           const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
@@ -277,7 +281,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
             continue;
           }
           const float w = __fmul_rn(e.alpha, T);
-          const float4 col = S.rec[j].col, nrm = S.rec[j].n;
+          const float4 col = S.rec.col[j], nrm = S.rec.n[j];
           C0 = __fmaf_rn(w, col.x, C0);
           C1 = __fmaf_rn(w, col.y, C1);
           C2 = __fmaf_rn(w, col.z, C2);
@@ -316,7 +320,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
           int nrel = 0;
           for (int wd = 0; wd < (count + 31) >> 5; wd++) {
             const int j = wd * 32 + lane;
-            const bool rel = j < count && in_rect(S.rec[j].rect, qx, qy);
+            const bool rel = j < count && in_rect(S.rec.rect[j], qx, qy);
             const uint32_t bb = __ballot_sync(0xffffffffu, rel);
             if (rel) S.list[wid][nrel + __popc(bb & lt_mask)] = (uint16_t)j;
             nrel += __popc(bb);
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
             Pair e;
             float alpha = 0.f;
             if (has) {
-              eval_pair(S.rec[j].c, S.rec[j].p, S.rec[j].q, fx, fy, P.lp_scale, P.alpha_max, e);
+              eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], fx, fy, P.lp_scale, P.alpha_max, e);
               alpha = e.alpha;
             }
             const bool kept = has && alpha >= P.alpha_min;
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
             const float w = contrib ? __fmul_rn(alpha, Tb) : 0.f;
             float vals[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (contrib) {
-              const float4 col = S.rec[j].col, nrm = S.rec[j].n;
+              const float4 col = S.rec.col[j], nrm = S.rec.n[j];
               vals[0] = w * col.x; vals[1] = w * col.y; vals[2] = w * col.z; vals[3] = w * col.w;
               vals[4] = w * nrm.x; vals[5] = w * nrm.y; vals[6] = w * nrm.z;
             }
@@ -453,31 +457,40 @@ __device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const
 // Dynamic shared memory of the backward kernel.
 template <int NT, int CHUNK>
 struct BwdSmem {
-  SRec rec[CHUNK];
+  static constexpr int RING = 2 * CHUNK;  // >= CHUNK + 32, a power of two
+  SRecs<CHUNK> rec;
   float grad[CHUNK * SGRAD_STRIDE];
   uint32_t idx[CHUNK];
-  uint16_t list[NT / 32][CHUNK];
-  float2 tq[NT];       // (T, Q) of each pixel between chunks
+  uint32_t pbits[NT][CHUNK / 32];  // per pixel: chunk entries whose rect holds it, below its last
+  float4 up[NT][2];                // per pixel: dC0 dC1 dC2 dD | dN0 dN1 dN2 dA*T_final
+  float2 tq[NT];                   // per pixel: (T in front of the deepest unprocessed entry, Q behind it)
+  uint32_t ring[NT / 32][RING];    // per warp: queued (pixel << 16 | entry), deepest entry first per pixel
   uint16_t apix[NT];
   int item, nact, next;
   uint32_t top;
 };
 
-// The reverse pass is entry-parallel throughout: per chunk, the tile's pixels
-// that still have entries in it are pulled by the warps one at a time; a warp
-// takes 32 of the pixel's entries per step (lane 0 the deepest), recovers the
-// transmittance in front of each by a prefix product of 1/(1 - alpha) and the
-// suffix sum behind each by a prefix sum, and every lane adds its own entry's
-// gradient to that entry's shared-memory slot.
+// The reverse pass streams (pixel, entry) pairs.  Per chunk, each warp
+// builds its 8x4 patch's per-pixel entry masks with ballots; then the warps
+// pull the tile's pixels that still have entries in the chunk and queue each
+// pixel's entries, deepest first, in a per-warp ring.  Every step takes the
+// next 32 queued pairs -- usually several pixels -- and evaluates them in
+// parallel: within each pixel's run (segments found with a ballot of run
+// starts), a segmented prefix product of 1/(1 - alpha) recovers the
+// transmittance in front of each entry and a segmented prefix sum gives the
+// sum behind it; every lane then adds its own pair's gradient terms to the
+// entry's shared-memory slot, and the last lane of each run stores the
+// pixel's running (T, Q) for its next run.
 template <int TW, int TH, int CHUNK>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(const RenderArgs A) {
-  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
+  constexpr int RING = BwdSmem<NT, CHUNK>::RING;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem<NT, CHUNK>& S = *reinterpret_cast<BwdSmem<NT, CHUNK>*>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t lt_mask = (1u << lane) - 1u;
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
+  uint32_t* ring = S.ring[wid];
   for (int i = threadIdx.x; i < CHUNK * SGRAD_STRIDE; i += NT) S.grad[i] = 0.f;
   for (;;) {
     if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_bwd, 1u);
@@ -489,21 +502,33 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(
     const DView& vw = A.views[v];
     const int lt = t - vw.tile_base;
     const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
-    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7);
-    const int ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
+    const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
+    const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
     const bool inside = ipx < vw.W && ipy < vw.H;
     const uint2 range = __ldg(A.ranges + t);
     const int64_t HW = (int64_t)vw.W * vw.H;
     uint32_t my_last = range.x;
     float T = 1.f, Q = 0.f;
-    if (inside) {
-      const int64_t pix = (int64_t)ipy * vw.W + ipx;
-      my_last = A.last[vw.poff + pix];
-      T = A.tfinal[vw.poff + pix];
-      if (A.d_rgb) {
-        const float* g = A.d_rgb + 3 * vw.poff + pix;
-        Q = T * (g[0] * P.bg[0] + g[HW] * P.bg[1] + g[2 * HW] * P.bg[2]);
+    {
+      float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
+      if (inside) {
+        const int64_t pix = (int64_t)ipy * vw.W + ipx;
+        my_last = A.last[vw.poff + pix];
+        T = A.tfinal[vw.poff + pix];
+        if (A.d_rgb) {
+          const float* g = A.d_rgb + 3 * vw.poff + pix;
+          u0.x = g[0]; u0.y = g[HW]; u0.z = g[2 * HW];
+        }
+        if (A.d_depth) u0.w = A.d_depth[vw.poff + pix];
+        if (A.d_normal) {
+          const float* g = A.d_normal + 3 * vw.poff + pix;
+          u1.x = g[0]; u1.y = g[HW]; u1.z = g[2 * HW];
+        }
+        if (A.d_alpha) u1.w = A.d_alpha[vw.poff + pix] * T;
+        Q = T * (u0.x * P.bg[0] + u0.y * P.bg[1] + u0.z * P.bg[2]);
       }
+      S.up[threadIdx.x][0] = u0;
+      S.up[threadIdx.x][1] = u1;
     }
     if (threadIdx.x == 0) S.top = range.x;
     __syncthreads();
@@ -513,13 +538,22 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(
     for (int64_t hi = top; hi > (int64_t)range.x; hi -= CHUNK) {
       const int64_t lo = max64((int64_t)range.x, hi - CHUNK);
       const int count = (int)(hi - lo);
-      const bool act = (int64_t)my_last > lo;
+      const int nwd = (count + 31) >> 5;
+      const bool act = inside && (int64_t)my_last > lo;
       if (threadIdx.x == 0) {
         S.nact = 0;
         S.next = 0;
       }
       stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx);
       __syncthreads();
+      // per-pixel masks of this chunk, restricted to the entries below the pixel's last
+      const int lim = act ? (int)min64((int64_t)my_last - lo, count) : 0;
+      for (int wd = 0; wd < nwd; wd++) {
+        uint32_t m = lane_word(S.rec, wd, count, bx, by, lane);
+        const int keep = lim - wd * 32;
+        m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
+        S.pbits[threadIdx.x][wd] = m;
+      }
       if (act) {
         const int k = atomicAdd(&S.nact, 1);
         S.apix[k] = (uint16_t)threadIdx.x;
@@ -527,82 +561,101 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(
       }
       __syncthreads();
       const int n_act = S.nact;
+      int head = 0, pending = 0;
+      bool more = true;
       for (;;) {
-        int k = 0;
-        if (lane == 0) k = atomicAdd(&S.next, 1);
-        k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= n_act) break;
-        const int pth = S.apix[k];
-        const int pw = pth >> 5, pl = pth & 31;
-        const int qx = tx0 + (pw % WX) * 8 + (pl & 7), qy = ty0 + (pw / WX) * 4 + (pl >> 3);
-        const float fx = (float)qx + 0.5f, fy = (float)qy + 0.5f;
-        const int64_t qpix = vw.poff + (int64_t)qy * vw.W + qx;
-        float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, e4 = 0.f, e5 = 0.f, e6 = 0.f, eA = 0.f;
-        if (A.d_rgb) {
-          const float* g = A.d_rgb + 3 * vw.poff + (int64_t)qy * vw.W + qx;
-          e0 = __ldg(g); e1 = __ldg(g + HW); e2 = __ldg(g + 2 * HW);
-        }
-        if (A.d_depth) e3 = __ldg(A.d_depth + qpix);
-        if (A.d_normal) {
-          const float* g = A.d_normal + 3 * vw.poff + (int64_t)qy * vw.W + qx;
-          e4 = __ldg(g); e5 = __ldg(g + HW); e6 = __ldg(g + 2 * HW);
-        }
-        if (A.d_alpha) eA = __ldg(A.d_alpha + qpix);
-        const float eAT = eA * A.tfinal[qpix];
-        const int jmax = (int)min64((int64_t)A.last[qpix] - lo, count);
-        float2 tq = S.tq[pth];
-        float tt = tq.x, qq_ = tq.y;
-        // this pixel's entries of the chunk below its last, ascending
-        int nrel = 0;
-        for (int wd = 0; wd < (jmax + 31) >> 5; wd++) {
-          const int j = wd * 32 + lane;
-          const bool rel = j < jmax && in_rect(S.rec[j].rect, qx, qy);
-          const uint32_t bb = __ballot_sync(0xffffffffu, rel);
-          if (rel) S.list[wid][nrel + __popc(bb & lt_mask)] = (uint16_t)j;
-          nrel += __popc(bb);
-        }
-        __syncwarp();
-        for (int gend = nrel; gend > 0; gend -= 32) {
-          const int idx = gend - 1 - lane;  // lane 0 = the deepest entry of this step
-          const bool has = idx >= 0;
-          const int j = has ? (int)S.list[wid][idx] : 0;
-          Pair e;
-          float alpha = 0.f;
-          if (has) {
-            eval_pair(S.rec[j].c, S.rec[j].p, S.rec[j].q, fx, fy, P.lp_scale, P.alpha_max, e);
-            alpha = e.alpha;
+        // queue pixels until a full step is pending
+        while (pending < 32 && more) {
+          int k = 0;
+          if (lane == 0) k = atomicAdd(&S.next, 1);
+          k = __shfl_sync(0xffffffffu, k, 0);
+          if (k >= n_act) {
+            more = false;
+            break;
           }
-          const bool kept = has && alpha >= P.alpha_min;
-          const float iom = kept ? rcp_approx(__fsub_rn(1.f, alpha)) : 1.f;
-          const float Tb = tt * warp_scan_mul(iom, lane);  // transmittance in front of this entry
-          const float w = kept ? alpha * Tb : 0.f;
-          float f = 0.f;
-          if (kept) {
-            const float4 col = S.rec[j].col, nrm = S.rec[j].n;
-            f = fmaf(e0, col.x, fmaf(e1, col.y, fmaf(e2, col.z, fmaf(e3, col.w,
-                fmaf(e4, nrm.x, fmaf(e5, nrm.y, e6 * nrm.z))))));
+          const uint32_t pth = S.apix[k];
+          for (int wd = nwd - 1; wd >= 0; wd--) {
+            const uint32_t bits = S.pbits[pth][wd];
+            if (!bits) continue;
+            if ((bits >> lane) & 1u) {
+              const int above = __popc(bits & ~((2u << lane) - 1u));  // deeper entries of this word
+              ring[(head + pending + above) & (RING - 1)] = (pth << 16) | (uint32_t)(wd * 32 + lane);
+            }
+            pending += __popc(bits);
           }
-          const float wf = w * f;
-          const float Sin = warp_scan_add(wf, lane);
-          const float Qb = qq_ + (Sin - wf);  // sum over the entries behind this one
-          n_eval += has ? 1u : 0u;
-          if (kept) {
-            n_blend++;
-            const float da = Tb * f - (Qb - eAT) * iom;
-            float g[16];
-            float gz;
-            pair_grads(e, S.rec[j].p, S.rec[j].q, da, w, e0, e1, e2, e3, e4, e5, e6, P.lp_scale, g, gz);
-            float* sg = S.grad + j * SGRAD_STRIDE;
+          __syncwarp();
+        }
+        if (pending == 0) break;
+        const int nstep = min(32, pending);
+        const bool has = lane < nstep;
+        const uint32_t pr = has ? ring[(head + lane) & (RING - 1)] : 0xffffffffu;
+        const uint32_t pth = pr >> 16;
+        const int j = (int)(pr & 0xffffu);
+        // runs of one pixel: starts and ends within this step
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, pr, 1);
+        const uint32_t nextp = __shfl_down_sync(0xffffffffu, pr, 1);
+        const bool start = has && (lane == 0 || (prev >> 16) != pth);
+        const bool end = has && (lane == nstep - 1 || (nextp >> 16) != pth);
+        const uint32_t starts = __ballot_sync(0xffffffffu, start);
+        const int s0 = 31 - __clz(starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
+        float2 tq = make_float2(1.f, 0.f);
+        float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
+        Pair e;
+        float alpha = 0.f;
+        if (has) {
+          tq = S.tq[pth];
+          u0 = S.up[pth][0];
+          u1 = S.up[pth][1];
+          const int pw = (int)pth >> 5, pl = (int)pth & 31;
+          const float fx = (float)(tx0 + (pw % WX) * 8 + (pl & 7)) + 0.5f;
+          const float fy = (float)(ty0 + (pw / WX) * 4 + (pl >> 3)) + 0.5f;
+          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], fx, fy, P.lp_scale, P.alpha_max, e);
+          alpha = e.alpha;
+        }
+        const bool kept = has && alpha >= P.alpha_min;
+        const float iom = kept ? rcp_approx(__fsub_rn(1.f, alpha)) : 1.f;
+        // segmented prefix product: transmittance in front of this entry
+        float x = iom;
 #pragma unroll
-            for (int q = 0; q < 16; q++)
-              if (g[q] != 0.f) atomicAdd(sg + q, g[q]);
-            if (gz != 0.f) atomicAdd(sg + 16, gz);
-          }
-          tt = __shfl_sync(0xffffffffu, Tb, min(31, gend - 1));
-          qq_ += __shfl_sync(0xffffffffu, Sin, 31);
+        for (int o = 1; o < 32; o <<= 1) {
+          const float y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane - o >= s0) x = __fmul_rn(x, y);
         }
-        if (lane == 0) S.tq[pth] = make_float2(tt, qq_);
+        const float Tb = tq.x * x;
+        const float w = kept ? alpha * Tb : 0.f;
+        float f = 0.f;
+        if (kept) {
+          const float4 col = S.rec.col[j], nrm = S.rec.n[j];
+          f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, fmaf(u0.w, col.w,
+              fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, u1.z * nrm.z))))));
+        }
+        const float wf = w * f;
+        // segmented prefix sum: the sum over entries behind this one
+        float sum = wf;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const float y = __shfl_up_sync(0xffffffffu, sum, o);
+          if (lane - o >= s0) sum += y;
+        }
+        const float Qb = tq.y + (sum - wf);
+        n_eval += has ? 1u : 0u;
+        if (kept) {
+          n_blend++;
+          const float da = Tb * f - (Qb - u1.w) * iom;
+          float g[16];
+          float gz;
+          pair_grads(e, S.rec.p[j], S.rec.q[j], da, w, u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, P.lp_scale, g, gz);
+          float* sg = S.grad + j * SGRAD_STRIDE;
+#pragma unroll
+          for (int q = 0; q < 16; q++)
+            if (g[q] != 0.f) atomicAdd(sg + q, g[q]);
+          if (gz != 0.f) atomicAdd(sg + 16, gz);
+        }
         __syncwarp();
+        if (end) S.tq[pth] = make_float2(Tb, tq.y + sum);
+        __syncwarp();
+        head = (head + nstep) & (RING - 1);
+        pending -= nstep;
       }
       __syncthreads();
       if (act) {
@@ -611,13 +664,13 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(
         Q = tq.y;
       }
       // flush this chunk's per-entry sums: one set of vector atomics per entry
-      for (int j = threadIdx.x; j < count; j += NT) {
-        float* sg = S.grad + j * SGRAD_STRIDE;
+      for (int jj = threadIdx.x; jj < count; jj += NT) {
+        float* sg = S.grad + jj * SGRAD_STRIDE;
         float acc = 0.f;
 #pragma unroll
         for (int q = 0; q < 17; q++) acc += fabsf(sg[q]);
         if (acc != 0.f) {
-          float* dst = A.rgrad + (int64_t)S.idx[j] * GRAD_F;
+          float* dst = A.rgrad + (int64_t)S.idx[jj] * GRAD_F;
           red_add_v4(dst + 0, sg[0], sg[1], sg[2], sg[3]);
           red_add_v4(dst + 4, sg[4], sg[5], sg[6], sg[7]);
           red_add_v4(dst + 8, sg[8], sg[9], sg[10], sg[11]);
@@ -712,6 +765,7 @@ static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
       if (CH == 64) return FN<16, 16, 64>(__VA_ARGS__);                       \
       if (CH == 128) return FN<16, 16, 128>(__VA_ARGS__);                     \
       if (CH == 256) return FN<16, 16, 256>(__VA_ARGS__);                     \
+      if (CH == 512) return FN<16, 16, 512>(__VA_ARGS__);                     \
     } else if (TWv == 8 && THv == 8) {                                        \
       if (CH == 64) return FN<8, 8, 64>(__VA_ARGS__);                         \
       if (CH == 128) return FN<8, 8, 128>(__VA_ARGS__);                       \
@@ -720,6 +774,7 @@ static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
       if (CH == 64) return FN<32, 8, 64>(__VA_ARGS__);                        \
       if (CH == 128) return FN<32, 8, 128>(__VA_ARGS__);                      \
       if (CH == 256) return FN<32, 8, 256>(__VA_ARGS__);                      \
+      if (CH == 512) return FN<32, 8, 512>(__VA_ARGS__);                      \
     }                                                                         \
     return cudaErrorInvalidValue;                                             \
   } while (0)

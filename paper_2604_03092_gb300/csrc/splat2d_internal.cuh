@@ -118,6 +118,7 @@ struct RastParams {
   float bg[3];
   int32_t tile_w, tile_h;
   int32_t stats;    // keep pair counters
+  int32_t fwd_tail; // forward: share the tile's pixels across warps below this many active per warp
 };
 
 // ---------------------------------------------------------------------------

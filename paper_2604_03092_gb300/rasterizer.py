@@ -34,6 +34,7 @@ class RasterConfig:
     z_near: float = 0.01
     bg: tuple = (0.0, 0.0, 0.0)
     stats: bool = True
+    fwd_tail: int = 0  # 0: default; 255: forward always shares pixels across warps
 
     def to_c(self) -> _abi.Config:
         c = _abi.Config()
@@ -42,7 +43,7 @@ class RasterConfig:
         c.lowpass_sigma, c.z_near = self.lowpass_sigma, self.z_near
         for i in range(3):
             c.bg[i] = float(self.bg[i])
-        c.flags = 0 if self.stats else _abi.FLAG_NO_STATS
+        c.flags = (0 if self.stats else _abi.FLAG_NO_STATS) | ((int(self.fwd_tail) & 0xFF) << 8)
         return c
 
 
