@@ -230,19 +230,18 @@ def main():
     import torch
     import torch.distributed as dist
 
-    from paper_2604_03092_gb300 import autotune
+    from paper_2604_03092_gb300 import autotune, multirank
     from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ri = multirank.rank_info()
+    world, rank, local = ri.world, ri.rank, ri.local
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
 
-    sc = make(rank)  # each rank: its own independent submap
+    sc = make(multirank.submap_seed_offset(rank))  # each rank: its own independent submap
     V = len(sc.views)
     params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
               (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
@@ -315,8 +314,7 @@ def main():
     except Exception:
         pass
     launches0 = rast.launch_count()
-    if world > 1:
-        dist.barrier()
+    multirank.barrier()
     torch.cuda.synchronize()
     with ClockSampler(uuid) as clk:
         t_start.record()
@@ -325,21 +323,17 @@ def main():
         t_end.record()
         torch.cuda.synchronize()
     launches = rast.launch_count() - launches0
-    if world > 1:
-        dist.barrier()
+    multirank.barrier()
     elapsed_ms = t_start.elapsed_time(t_end)
     stage_ms = {s: float(np.mean([evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(args.steps)]))
                 for i, s in enumerate(stages)}
     st = rast.stats()
     if st["status"] != 0:
         raise SystemExit(f"device status {st['status']} in the timed region")
-    max_ms = elapsed_ms
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        max_ms = float(t.item())
+    max_ms = multirank.max_over_ranks(elapsed_ms, dev)
+    views_all = multirank.sum_over_ranks(V * args.steps, dev)
     ms_per_step = max_ms / args.steps
-    value = world * V * args.steps / (max_ms / 1e3)
+    value = multirank.whole_job_rate(views_all, max_ms)
 
     # ---- the same step replayed from a CUDA graph ----------------------------
     graph_vps = None
@@ -411,11 +405,8 @@ def main():
     b.record()
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b)
-    e2e_vps = V * args.e2e_steps / (e2e_ms / 1e3)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_vps = world * V * args.e2e_steps / (float(t.item()) / 1e3)
+    e2e_vps = multirank.whole_job_rate(multirank.sum_over_ranks(V * args.e2e_steps, dev),
+                                       multirank.max_over_ranks(e2e_ms, dev))
 
     # ---- roofline of the dominant stage ------------------------------------------
     peaks = _peaks()
