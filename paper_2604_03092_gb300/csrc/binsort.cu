@@ -92,15 +92,30 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
   }
 }
 
+// Size classes of the per-tile bucket sorts (upper bounds, inclusive; longer
+// buckets go with the last class).
+constexpr int SORT_CLASS_S = 1024;
+constexpr int SORT_CLASS_M = 4096;
+constexpr int SORT_CLASS_L = 12288;
+
+__device__ __forceinline__ int sort_class(uint32_t n) {
+  return n == 0 ? -1 : (n <= (uint32_t)SORT_CLASS_S ? 0 : (n <= (uint32_t)SORT_CLASS_M ? 1 : 2));
+}
+
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
-// total and the capacity check.
+// total and the capacity check; every non-empty tile is appended to the list
+// of its sort size class.
+
 __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ counts, uint2* __restrict__ ranges,
-                                                    int64_t T, Header* __restrict__ hdr, int64_t cap) {
+                                                    int64_t T, Header* __restrict__ hdr, int64_t cap,
+                                                    uint32_t* __restrict__ class_list,
+                                                    uint32_t* __restrict__ class_count) {
   __shared__ unsigned long long s_w[32];
   __shared__ unsigned long long s_carry;
   if (threadIdx.x == 0) s_carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
   for (int64_t base = 0; base < T; base += 1024) {
     const int64_t i = base + threadIdx.x;
     const unsigned long long v = i < T ? counts[i] : 0ull;
@@ -122,10 +137,21 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ count
     __syncthreads();
     const unsigned long long incl = x + (wid > 0 ? s_w[wid - 1] : 0ull) + s_carry;
     const unsigned long long start = incl - v;
+    const bool fits = incl <= (unsigned long long)cap;
     if (i < T) {
-      const bool fits = incl <= (unsigned long long)cap;
       ranges[i] = fits ? make_uint2((uint32_t)start, (uint32_t)incl) : make_uint2(0u, 0u);
       counts[i] = fits ? (uint32_t)start : 0u;
+    }
+    // append the tile to its size class's list (order within a list is free)
+    const int cls = (i < T && fits) ? sort_class((uint32_t)v) : -1;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const uint32_t m = __ballot_sync(0xffffffffu, cls == c);
+      if (!m) continue;
+      uint32_t at = 0;
+      if (lane == 0) at = atomicAdd(&class_count[c], (uint32_t)__popc(m));
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (cls == c) class_list[(size_t)c * T + at + __popc(m & lt_mask)] = (uint32_t)i;
     }
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = incl;
@@ -143,32 +169,42 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ count
   }
 }
 
-// Stable LSD radix sort of `n` composite keys by their depth bits (high 32),
-// 8 bits per pass, ping-ponging between a and b (generic pointers: shared or
-// global memory), ranked per warp with match_any so that equal digits keep
-// their order.  4 passes: the result ends in `a`.  Needs NWARPS*256 counters.
+// Number of bits needed to represent v (0 for v == 0).
+__device__ __forceinline__ int bits_of(uint32_t v) { return v ? 32 - __clz(v) : 0; }
+
+// Stable LSD radix sort of n composite keys (depth bits << 32 | surfel index)
+// in place in `a` (b: scratch of the same size), 8-bit digits of
+// key_of(x) = ((x >> 32) - dmin) << ishift | ((x & 0xffffffff) - imin) over
+// `nbits` bits (ishift < 0: the depth part alone, key_of(x) = (x >> 32) - dmin); generic pointers (shared or global memory); ranked per warp
+// with match_any so that equal digits keep their order.  `cnt` holds
+// (NWARPS + 1) * 256 counters.  Returns with the result in `a`.
 template <int NWARPS>
-__device__ void block_sort_depth(unsigned long long* a, unsigned long long* b, int n, uint32_t* cnt) {
+__device__ void block_radix_any(unsigned long long* a, unsigned long long* b, int n, uint32_t* cnt, uint32_t dmin,
+                            uint32_t imin, int ishift, int nbits) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int per = (((n + NWARPS - 1) / NWARPS) + 31) & ~31;  // elements per warp, whole rounds
   const int lo = min(wid * per, n), hi = min(lo + per, n);
-  for (int pass = 0; pass < 4; pass++) {
-    const int shift = 32 + 8 * pass;
-    unsigned long long* src = (pass & 1) ? b : a;
-    unsigned long long* dst = (pass & 1) ? a : b;
+  const int passes = (nbits + 7) >> 3;
+  unsigned long long* src = a;
+  unsigned long long* dst = b;
+  auto digit = [&](unsigned long long x, int shift) -> uint32_t {
+    const unsigned long long dk = (unsigned long long)((uint32_t)(x >> 32) - dmin);
+    const unsigned long long k = ishift < 0 ? dk : ((dk << ishift) | (unsigned long long)((uint32_t)x - imin));
+    return (uint32_t)(k >> shift) & 0xffu;
+  };
+  for (int pass = 0; pass < passes; pass++) {
+    const int shift = 8 * pass;
     for (int i = threadIdx.x; i < NWARPS * 256; i += NWARPS * 32) cnt[i] = 0;
     __syncthreads();
-    // per-warp digit counts
     for (int base = lo; base < hi; base += 32) {
       const int i = base + lane;
-      const uint32_t d = i < hi ? (uint32_t)(src[i] >> shift) & 0xffu : 256u;
+      const uint32_t d = i < hi ? digit(src[i], shift) : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       if (d < 256 && lane == __ffs(peers) - 1) cnt[wid * 256 + d] += __popc(peers);
       __syncwarp();
     }
     __syncthreads();
-    // exclusive offsets, digit-major then warp
     if (threadIdx.x < 256) {
       uint32_t acc = 0;
       for (int w = 0; w < NWARPS; w++) {
@@ -176,22 +212,21 @@ __device__ void block_sort_depth(unsigned long long* a, unsigned long long* b, i
         cnt[w * 256 + threadIdx.x] = acc;
         acc += c;
       }
-      cnt[NWARPS * 256 + threadIdx.x] = acc;  // digit total
+      cnt[NWARPS * 256 + threadIdx.x] = acc;
     }
     __syncthreads();
     if (threadIdx.x < 32) {
-      // exclusive scan of the 256 digit totals, 8 per lane
-      uint32_t v[8], s = 0;
+      uint32_t v[8], sum = 0;
       for (int k = 0; k < 8; k++) {
         v[k] = cnt[NWARPS * 256 + lane * 8 + k];
-        s += v[k];
+        sum += v[k];
       }
-      uint32_t x = s;
+      uint32_t x = sum;
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      uint32_t run = x - s;
+      uint32_t run = x - sum;
       for (int k = 0; k < 8; k++) {
         cnt[NWARPS * 256 + lane * 8 + k] = run;
         run += v[k];
@@ -203,11 +238,10 @@ __device__ void block_sort_depth(unsigned long long* a, unsigned long long* b, i
       for (int w = 0; w < NWARPS; w++) cnt[w * 256 + threadIdx.x] += dbase;
     }
     __syncthreads();
-    // stable scatter
     for (int base = lo; base < hi; base += 32) {
       const int i = base + lane;
       const unsigned long long key = i < hi ? src[i] : 0ull;
-      const uint32_t d = i < hi ? (uint32_t)(key >> shift) & 0xffu : 256u;
+      const uint32_t d = i < hi ? digit(key, shift) : 256u;
       const uint32_t peers = __match_any_sync(0xffffffffu, d);
       uint32_t pos = 0;
       if (d < 256) pos = cnt[wid * 256 + d];
@@ -219,14 +253,55 @@ __device__ void block_sort_depth(unsigned long long* a, unsigned long long* b, i
       __syncwarp();
     }
     __syncthreads();
+    unsigned long long* tmp = src;
+    src = dst;
+    dst = tmp;
   }
-  // equal depth bits: ascending surfel index (runs are short)
+  if (src != a) {
+    for (int i = threadIdx.x; i < n; i += NWARPS * 32) a[i] = src[i];
+    __syncthreads();
+  }
+}
+
+// Sort one tile's bucket by (depth bits, surfel index).  The depth digits are
+// taken relative to the bucket's smallest depth, so only the bits that vary
+// are sorted; equal depths are then put in surfel order, and a bucket with a
+// long run of equal depths is sorted once more on the full composite key.
+template <int NWARPS>
+__device__ void sort_bucket_any(unsigned long long* a, unsigned long long* b, int n, uint32_t* cnt, uint32_t* red) {
+  // red[0..3]: min depth, max depth, min index, max index; red[4]: long-run flag
+  if (threadIdx.x == 0) {
+    red[0] = 0xffffffffu; red[1] = 0u; red[2] = 0xffffffffu; red[3] = 0u; red[4] = 0u;
+  }
+  __syncthreads();
+  uint32_t dmn = 0xffffffffu, dmx = 0u, imn = 0xffffffffu, imx = 0u;
+  for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
+    const unsigned long long x = a[i];
+    const uint32_t d = (uint32_t)(x >> 32), s = (uint32_t)x;
+    dmn = min(dmn, d); dmx = max(dmx, d); imn = min(imn, s); imx = max(imx, s);
+  }
+  dmn = __reduce_min_sync(0xffffffffu, dmn);
+  dmx = __reduce_max_sync(0xffffffffu, dmx);
+  imn = __reduce_min_sync(0xffffffffu, imn);
+  imx = __reduce_max_sync(0xffffffffu, imx);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&red[0], dmn); atomicMax(&red[1], dmx); atomicMin(&red[2], imn); atomicMax(&red[3], imx);
+  }
+  __syncthreads();
+  const uint32_t dmin = red[0], dbits = (uint32_t)bits_of(red[1] - red[0]);
+  const uint32_t imin = red[2], ibits = (uint32_t)bits_of(red[3] - red[2]);
+  block_radix_any<NWARPS>(a, b, n, cnt, dmin, 0u, -1, (int)dbits);
+  // equal depth bits: ascending surfel index (short runs in place)
   for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
     const uint32_t d = (uint32_t)(a[i] >> 32);
     const bool starts = (i == 0 || (uint32_t)(a[i - 1] >> 32) != d) && i + 1 < n && (uint32_t)(a[i + 1] >> 32) == d;
     if (!starts) continue;
     int e = i + 1;
-    while (e + 1 < n && (uint32_t)(a[e + 1] >> 32) == d) e++;
+    while (e + 1 < n && e - i < 64 && (uint32_t)(a[e + 1] >> 32) == d) e++;
+    if (e + 1 < n && (uint32_t)(a[e + 1] >> 32) == d) {
+      red[4] = 1u;  // a long run: handled below
+      continue;
+    }
     for (int x = i + 1; x <= e; x++) {
       const unsigned long long key = a[x];
       int y = x - 1;
@@ -238,53 +313,249 @@ __device__ void block_sort_depth(unsigned long long* a, unsigned long long* b, i
     }
   }
   __syncthreads();
+  if (red[4]) block_radix_any<NWARPS>(a, b, n, cnt, dmin, imin, (int)ibits, (int)(dbits + ibits));
 }
 
-constexpr int SEG_THREADS = 512;
-constexpr int SEG_WARPS = SEG_THREADS / 32;
-constexpr int SEG_SMEM_KEYS = 12288;  // keys per shared-memory bucket sort (two buffers)
-constexpr size_t SEG_SMEM_BYTES = 2 * sizeof(unsigned long long) * SEG_SMEM_KEYS + sizeof(uint32_t) * (SEG_WARPS + 1) * 256;
+// Shared-memory radix sort of a bucket of at most NWARPS * 32 * ITEMS
+// composites, the keys of each pass held in registers.  Warp w owns a
+// contiguous slice of the array; per pass it ranks its keys round by round
+// (a round = 32 consecutive keys) with a ballot multisplit: eight ballots, one
+// per digit bit, give each lane the mask of lanes holding its digit, so the
+// rank within the round is a population count, and the round's first lane of
+// each digit advances the warp's 16-bit counter of that digit.  A block scan
+// of the (digit, warp) counters in digit-major order turns them into output
+// offsets, so equal digits keep their order (stable), and every key is then
+// stored at its offset.  Digits are those of block_radix_any.  Returns the
+// buffer holding the result (a or b).
+template <int NWARPS>
+struct RegSortSmem {
+  static constexpr int CP = NWARPS + 2;  // padded counter row: conflict-free leader updates
+  static constexpr size_t CNT_BYTES = sizeof(uint16_t) * 256 * CP;
+  static constexpr size_t BYTES = ((CNT_BYTES + 15) & ~(size_t)15) + sizeof(uint32_t) * (32 + 8);
+};
 
+template <int NWARPS, int ITEMS>
+__device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned long long* b, int n, uint16_t* cnt,
+                                               uint32_t* tot, uint32_t dmin, uint32_t imin, int ishift, int nbits) {
+  constexpr int NT = NWARPS * 32, CP = RegSortSmem<NWARPS>::CP;
+  static_assert(NWARPS % 8 == 0, "the counter scan takes 8 counters per thread");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const int per = (((n + NWARPS - 1) / NWARPS) + 31) & ~31;
+  const int lo = min(wid * per, n), hi = min(lo + per, n);
+  const int nr = (hi - lo + 31) >> 5;  // rounds of this warp (<= ITEMS)
+  const int passes = (nbits + 7) >> 3;
+  unsigned long long* src = a;
+  unsigned long long* dst = b;
+  for (int pass = 0; pass < passes; pass++) {
+    const int shift = 8 * pass;
+    unsigned long long key[ITEMS];
+    uint32_t off[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+      const int i = lo + k * 32 + lane;
+      key[k] = (k < nr && i < hi) ? src[i] : 0ull;
+    }
+    for (int i = threadIdx.x; i < 256 * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+      if (k < nr) {
+        const bool valid = lo + k * 32 + lane < hi;
+        uint32_t d = 0;
+        if (valid) {
+          const unsigned long long dk = (unsigned long long)((uint32_t)(key[k] >> 32) - dmin);
+          const unsigned long long kk =
+              ishift < 0 ? dk : ((dk << ishift) | (unsigned long long)((uint32_t)key[k] - imin));
+          d = (uint32_t)(kk >> shift) & 0xffu;
+        }
+        uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+        for (int bit = 0; bit < 8; bit++) {
+          const bool on = (d >> bit) & 1u;
+          const uint32_t bal = __ballot_sync(0xffffffffu, on);
+          peers &= on ? bal : ~bal;
+        }
+        const int leader = __ffs(peers) - 1;
+        uint32_t pre = 0;
+        if (valid && lane == leader) {
+          pre = cnt[d * CP + wid];
+          cnt[d * CP + wid] = (uint16_t)(pre + __popc(peers));
+        }
+        pre = __shfl_sync(0xffffffffu, pre, leader & 31);
+        off[k] = (d << 16) | (pre + __popc(peers & lt_mask));
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    {
+      // exclusive scan of the counters in (digit, warp) order, 8 per thread
+      const int f0 = 8 * threadIdx.x, d = f0 / NWARPS, w0 = f0 % NWARPS;
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        c[j] = cnt[d * CP + w0 + j];
+        sum += c[j];
+      }
+      uint32_t x = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) tot[wid] = x;
+      __syncthreads();
+      if (wid == 0) {
+        uint32_t y = lane < NWARPS ? tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+          if (lane >= o) y += z;
+        }
+        if (lane < NWARPS) tot[lane] = y;
+      }
+      __syncthreads();
+      uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        cnt[d * CP + w0 + j] = (uint16_t)ex;
+        ex += c[j];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+      if (k < nr && lo + k * 32 + lane < hi) {
+        const uint32_t d = off[k] >> 16;
+        dst[(uint32_t)cnt[d * CP + wid] + (off[k] & 0xffffu)] = key[k];
+      }
+    }
+    __syncthreads();
+    unsigned long long* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
+// Sort a bucket of at most NWARPS * 32 * ITEMS composites by (depth bits,
+// surfel index): load it from global memory into shared memory (finding the
+// bucket's depth and index ranges on the way), sort the depth bits relative
+// to the smallest depth, put equal depths in surfel order in place (a run of
+// more than 64 equal depths triggers one exact re-sort on the relative
+// composite key instead).  Returns the shared buffer holding the result.
+template <int NWARPS, int ITEMS>
+__device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restrict__ g, int n,
+                                               unsigned long long* sa, unsigned long long* sb, uint16_t* cnt,
+                                               uint32_t* tot, uint32_t* red) {
+  constexpr int NT = NWARPS * 32;
+  if (threadIdx.x == 0) {
+    red[0] = 0xffffffffu; red[1] = 0u; red[2] = 0xffffffffu; red[3] = 0u; red[4] = 0u;
+  }
+  __syncthreads();
+  uint32_t dmn = 0xffffffffu, dmx = 0u, imn = 0xffffffffu, imx = 0u;
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const unsigned long long x = g[i];
+    sa[i] = x;
+    const uint32_t d = (uint32_t)(x >> 32), s = (uint32_t)x;
+    dmn = min(dmn, d); dmx = max(dmx, d); imn = min(imn, s); imx = max(imx, s);
+  }
+  dmn = __reduce_min_sync(0xffffffffu, dmn);
+  dmx = __reduce_max_sync(0xffffffffu, dmx);
+  imn = __reduce_min_sync(0xffffffffu, imn);
+  imx = __reduce_max_sync(0xffffffffu, imx);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&red[0], dmn); atomicMax(&red[1], dmx); atomicMin(&red[2], imn); atomicMax(&red[3], imx);
+  }
+  __syncthreads();
+  const uint32_t dmin = red[0], dbits = (uint32_t)bits_of(red[1] - red[0]);
+  const uint32_t imin = red[2], ibits = (uint32_t)bits_of(red[3] - red[2]);
+  unsigned long long* r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits);
+  for (int i = threadIdx.x; i < n; i += NT) {
+    const uint32_t d = (uint32_t)(r[i] >> 32);
+    const bool starts = (i == 0 || (uint32_t)(r[i - 1] >> 32) != d) && i + 1 < n && (uint32_t)(r[i + 1] >> 32) == d;
+    if (!starts) continue;
+    int e = i + 1;
+    while (e + 1 < n && e - i < 64 && (uint32_t)(r[e + 1] >> 32) == d) e++;
+    if (e + 1 < n && (uint32_t)(r[e + 1] >> 32) == d) {
+      red[4] = 1u;
+      continue;
+    }
+    for (int x = i + 1; x <= e; x++) {
+      const unsigned long long key = r[x];
+      int y = x - 1;
+      while (y >= i && r[y] > key) {
+        r[y + 1] = r[y];
+        y--;
+      }
+      r[y + 1] = key;
+    }
+  }
+  __syncthreads();
+  if (red[4])
+    r = block_radix_reg<NWARPS, ITEMS>(r, r == sa ? sb : sa, n, cnt, tot, dmin, imin, (int)ibits,
+                                       (int)(dbits + ibits));
+  return r;
+}
+
+// Per-tile bucket sorts in three size classes, each a persistent launch over
+// its class's tile list with shared memory sized for the class (so short
+// buckets run several CTAs per SM); the last class also takes the buckets
+// longer than its capacity and sorts those in global memory.
 struct SegArgs {
   const uint2* ranges;
-  int64_t T;
-  unsigned long long* bucket;   // scattered composites (sorted in place for the large buckets)
-  unsigned long long* scratch;  // ping-pong space for the large buckets (same indexing as bucket)
+  unsigned long long* bucket;   // scattered composites (sorted in place for the oversized buckets)
+  unsigned long long* scratch;  // ping-pong space for the oversized buckets (same indexing as bucket)
   uint64_t* keys;               // out: (tile << 32) | depth bits
   uint32_t* vals;               // out: surfel index
   const Header* hdr;
-  uint32_t* queue;              // work counter
+  const uint32_t* list;         // this class's tiles
+  const uint32_t* list_count;   // their number
+  uint32_t* queue;              // this class's work counter
 };
 
-__global__ void __launch_bounds__(SEG_THREADS) k_tile_sort(const SegArgs A) {
+template <int NWARPS, int ITEMS>
+struct SegClass {
+  static constexpr int THREADS = NWARPS * 32;
+  static constexpr int CAP = NWARPS * 32 * ITEMS;
+  static constexpr size_t SMEM = 2 * sizeof(unsigned long long) * CAP + RegSortSmem<NWARPS>::BYTES;
+  static_assert(2 * sizeof(unsigned long long) * CAP >= sizeof(uint32_t) * ((NWARPS + 1) * 256 + 8),
+                "the oversized-bucket counters fit in the key buffers");
+};
+
+template <int NWARPS, int ITEMS, bool LAST>
+__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 2 : 1) k_tile_sort(const SegArgs A) {
+  using C = SegClass<NWARPS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* sa = reinterpret_cast<unsigned long long*>(smem);
-  unsigned long long* sb = sa + SEG_SMEM_KEYS;
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(sb + SEG_SMEM_KEYS);
-  __shared__ int s_t;
+  unsigned long long* sb = sa + C::CAP;
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(sb + C::CAP);
+  uint32_t* tot = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(unsigned long long) * C::CAP +
+                                              ((RegSortSmem<NWARPS>::CNT_BYTES + 15) & ~(size_t)15));
+  uint32_t* red = tot + 32;
+  __shared__ uint32_t s_q;
   if (A.hdr->status != 0) return;
+  const uint32_t n_tiles = *A.list_count;
   for (;;) {
-    if (threadIdx.x == 0) s_t = (int)atomicAdd(A.queue, 1u);
+    if (threadIdx.x == 0) s_q = atomicAdd(A.queue, 1u);
     __syncthreads();
-    const int t = s_t;
+    const uint32_t q = s_q;
     __syncthreads();
-    if (t >= A.T) break;
+    if (q >= n_tiles) break;
+    const uint32_t t = A.list[q];
     const uint2 rg = A.ranges[t];
     const int n = (int)(rg.y - rg.x);
-    if (n == 0) continue;
-    unsigned long long* src;
-    if (n <= SEG_SMEM_KEYS) {
-      for (int i = threadIdx.x; i < n; i += SEG_THREADS) sa[i] = A.bucket[rg.x + i];
-      __syncthreads();
-      block_sort_depth<SEG_WARPS>(sa, sb, n, cnt);
-      src = sa;
+    const unsigned long long* res;
+    if (!LAST || n <= C::CAP) {
+      res = sort_bucket_reg<NWARPS, ITEMS>(A.bucket + rg.x, n, sa, sb, cnt, tot, red);
     } else {
-      block_sort_depth<SEG_WARPS>(A.bucket + rg.x, A.scratch + rg.x, n, cnt);
-      src = A.bucket + rg.x;
+      uint32_t* c32 = reinterpret_cast<uint32_t*>(smem);
+      sort_bucket_any<NWARPS>(A.bucket + rg.x, A.scratch + rg.x, n, c32, c32 + (NWARPS + 1) * 256);
+      res = A.bucket + rg.x;
     }
     const uint64_t tile = (uint64_t)t << 32;
-    for (int i = threadIdx.x; i < n; i += SEG_THREADS) {
-      const unsigned long long key = src[i];
+    for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
+      const unsigned long long key = res[i];
       A.keys[rg.x + i] = tile | (key >> 32);
       A.vals[rg.x + i] = (uint32_t)key;
     }
@@ -292,13 +563,23 @@ __global__ void __launch_bounds__(SEG_THREADS) k_tile_sort(const SegArgs A) {
   }
 }
 
+template <int NWARPS, int ITEMS, bool LAST>
+static cudaError_t launch_tile_sort_class(const SegArgs& S, cudaStream_t st) {
+  using C = SegClass<NWARPS, ITEMS>;
+  auto k = k_tile_sort<NWARPS, ITEMS, LAST>;
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::THREADS, C::SMEM);
+    if (per_sm < 1) per_sm = 1;
+  }
+  k<<<per_sm * sm_count(), C::THREADS, C::SMEM, st>>>(S);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cudaStream_t st) {
   if (L.R <= 0 || L.T <= 0) return cudaSuccess;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_tile_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM_BYTES);
-    attr_set = true;
-  }
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
   uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.tile_count);
   uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
@@ -318,24 +599,31 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 16);
   k_tile_pass<false><<<grid, 256, 0, st>>>(A);
   count_launches(1);
-  k_tile_scan<<<1, 1024, 0, st>>>(counts, ranges, L.T, hdr, L.cap);
+  uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // 3 queues, 3 list sizes
+  uint32_t* class_list = reinterpret_cast<uint32_t*>(ws + L.tile_class);
+  e = cudaMemsetAsync(queues, 0, 6 * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  k_tile_scan<<<1, 1024, 0, st>>>(counts, ranges, L.T, hdr, L.cap, class_list, queues + 3);
   count_launches(1);
   k_tile_pass<true><<<grid, 256, 0, st>>>(A);
   count_launches(1);
   SegArgs S;
   S.ranges = ranges;
-  S.T = L.T;
   S.bucket = A.bucket;
   S.scratch = reinterpret_cast<unsigned long long*>(ws + L.keys0);
   S.keys = reinterpret_cast<uint64_t*>(ws + L.keys0);
   S.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
   S.hdr = hdr;
-  S.queue = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;
-  e = cudaMemsetAsync(S.queue, 0, sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
-  const int sgrid = (int)min64(L.T, (int64_t)sm_count());
-  k_tile_sort<<<sgrid, SEG_THREADS, SEG_SMEM_BYTES, st>>>(S);
-  count_launches(1);
+  static_assert(SegClass<8, 4>::CAP == SORT_CLASS_S && SegClass<16, 8>::CAP == SORT_CLASS_M &&
+                    SegClass<32, 12>::CAP == SORT_CLASS_L, "class capacities match the class bounds");
+  for (int c = 0; c < 3; c++) {
+    S.list = class_list + (size_t)c * L.T;
+    S.list_count = queues + 3 + c;
+    S.queue = queues + c;
+    e = c == 0 ? launch_tile_sort_class<8, 4, false>(S, st)
+               : (c == 1 ? launch_tile_sort_class<16, 8, false>(S, st) : launch_tile_sort_class<32, 12, true>(S, st));
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 

@@ -482,7 +482,7 @@ struct BwdSmem {
 // entry's shared-memory slot, and the last lane of each run stores the
 // pixel's running (T, Q) for its next run.
 template <int TW, int TH, int CHUNK>
-__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 8 : 2) k_render_bwd(const RenderArgs A) {
+__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 8) : 2) k_render_bwd(const RenderArgs A) {
   constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
   constexpr int RING = BwdSmem<NT, CHUNK>::RING;
   extern __shared__ __align__(16) unsigned char smem_raw[];

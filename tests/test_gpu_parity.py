@@ -109,9 +109,9 @@ def test_preprocess_matches_oracle(seed):
     assert np.array_equal(nt[vis_g], (tx * ty)[vis_g])
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
-def test_bin_sort_matches_oracle_bit_exact(tile):
-    sc = scenes.random_scene(n=3000, width=100, height=70, f=70.0, seed=4, n_views=3)
+def _check_bin_sort(sc, tile):
+    V = len(sc.views)
+    W, H = sc.views[0].width, sc.views[0].height
     cfg = RasterConfig(tile_w=tile[0], tile_h=tile[1])
     rast, params, _ = gpu_forward(sc, cfg)
     st = rast.stats()
@@ -120,10 +120,10 @@ def test_bin_sort_matches_oracle_bit_exact(tile):
     keys = rast.ws_tensor(lay.keys, n, torch.int64).cpu().numpy().view(np.uint64)
     vals = rast.ws_tensor(lay.vals, n, torch.int32).cpu().numpy().view(np.uint32)
     ocfg = oracle_cfg(cfg)
-    preps = [oracle.preprocess_scene_view(sc, v, ocfg) for v in range(3)]
-    tx = (100 + tile[0] - 1) // tile[0]
-    ty = (70 + tile[1] - 1) // tile[1]
-    okeys, ovals = oracle.bin_sort(preps, [0, tx * ty, 2 * tx * ty], [tx] * 3, [0, 0, 0])
+    preps = [oracle.preprocess_scene_view(sc, v, ocfg) for v in range(V)]
+    tx = (W + tile[0] - 1) // tile[0]
+    ty = (H + tile[1] - 1) // tile[1]
+    okeys, ovals = oracle.bin_sort(preps, [v * tx * ty for v in range(V)], [tx] * V, [0] * V)
     # drop (view, surfel) pairs whose tile rect is decided within rounding
     bad = set()
     for v, p in enumerate(preps):
@@ -139,7 +139,28 @@ def test_bin_sort_matches_oracle_bit_exact(tile):
     ok_, ov = keep(okeys, ovals)
     assert len(gk) == len(ok_)
     assert np.array_equal(gk, ok_) and np.array_equal(gv, ov)
-    assert len(bad) <= 0.01 * sc.n * 3
+    assert len(bad) <= 0.01 * sc.n * V
+    return np.bincount((okeys >> np.uint64(32)).astype(np.int64), minlength=V * tx * ty)
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8), (32, 8)])
+def test_bin_sort_matches_oracle_bit_exact(tile):
+    sc = scenes.random_scene(n=3000, width=100, height=70, f=70.0, seed=4, n_views=3)
+    _check_bin_sort(sc, tile)
+
+
+@pytest.mark.parametrize("n,tile", [(2500, (16, 16)), (9000, (16, 16)), (30000, (16, 16)), (30000, (8, 8))])
+def test_bin_sort_long_buckets_and_equal_depths(n, tile):
+    # every surfel covers the image centre, so the central tiles hold close to
+    # n entries: the per-tile sort runs its middle and large size classes and,
+    # above 12288 entries, its global-memory path; half of the surfels share
+    # one depth exactly (identity pose: the depth key is the centre's z), so
+    # the buckets hold runs of equal depth far longer than 64
+    sc = scenes.random_scene(n=n, width=64, height=48, f=60.0, seed=11, xy_range=0.3, scale_range=(0.2, 0.5),
+                             n_views=1, with_target=False)
+    sc.means[::2, 2] = np.float32(3.0)
+    counts = _check_bin_sort(sc, tile)
+    assert counts.max() > {2500: 1024, 9000: 4096, 30000: 12288}[n]
 
 
 # --------------------------------------------------------------------------
