@@ -208,9 +208,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="submap32")
-    ap.add_argument("--tile", default=None, help="WxH, e.g. 16x16 (default: autotune cache or 16x16)")
+    ap.add_argument("--tile", default=None, help="WxH, e.g. 16x16 (default: autotune cache, else the shipped GB300 measurement, else 8x8)")
     ap.add_argument("--chunk", type=int, default=None)
     ap.add_argument("--fwd-tail", type=int, default=None, help="forward tail threshold per warp (255 = always)")
+    ap.add_argument("--bwd-chunk", type=int, default=None, help="chunk of the backward pass (default: --chunk)")
     ap.add_argument("--plain-steps", type=int, default=2, help="steps of the per-view plain-launch baseline (0=skip)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-pixels", type=int, default=8192, help="pixels of the oracle CPU-baseline sample")
@@ -249,13 +250,15 @@ def main():
     cfg = RasterConfig(stats=True)
     tuned = autotune.lookup(sc.views, sc.n) if args.tile is None else None
     if tuned:
-        cfg.tile_w, cfg.tile_h, cfg.chunk = tuned
+        cfg.tile_w, cfg.tile_h, cfg.chunk, cfg.bwd_chunk = tuned
     if args.tile:
         cfg.tile_w, cfg.tile_h = (int(x) for x in args.tile.lower().split("x"))
     if args.chunk:
         cfg.chunk = args.chunk
     if args.fwd_tail is not None:
         cfg.fwd_tail = args.fwd_tail
+    if args.bwd_chunk is not None:
+        cfg.bwd_chunk = args.bwd_chunk
     rast = Rasterizer(sc.views, sc.n, cfg, device=dev)
     im = rast.forward(*params)  # sizes the instance capacity (synchronises once)
     st0 = rast.stats()
@@ -416,7 +419,9 @@ def main():
     n_inst = st["n_instances"]
     passes = (32 + max(int(lay.n_tiles - 1).bit_length(), 0) + 7) // 8
     work = {
-        "preprocess": ("hbm", 56 * sum(1 for _ in [0]) * rast.n_surfels + 4 * lay.n_records + 160 * n_vis),
+        # parameters read once per surfel (all views of a workload form one group), a tile count per
+        # (view, surfel) record, an 80-byte render record per visible pair
+        "preprocess": ("hbm", 56 * rast.n_surfels + 4 * lay.n_records + 80 * n_vis),
         "bin_sort": ("hbm", 8 * lay.n_records + 32 * n_vis + 8 * n_inst + 20 * n_inst),
         "render_fwd": ("alu", FLOP_EVAL * st["fwd_pairs_evaluated"] + FLOP_BLEND * st["fwd_pairs_blended"]),
         "render_bwd": ("alu", FLOP_EVAL * st["bwd_pairs_evaluated"] + FLOP_BWD * st["bwd_pairs_blended"]),
@@ -467,7 +472,8 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ray-cast indoor submap; stands in for ScanNet/BundleFusion)",
             "config": {"workload": args.workload, "description": wl_desc, "views": V, "surfels": sc.n,
-                       "tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk, "fwd_tail": cfg.fwd_tail, "instances": n_inst,
+                       "tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk,
+                       "bwd_chunk": cfg.bwd_chunk or cfg.chunk, "fwd_tail": cfg.fwd_tail, "instances": n_inst,
                        "visible_pairs": n_vis, "l2": "inputs larger than L2 (records + instances > 129 MB)",
                        "parallelism": f"{world} independent submap(s), one per GPU"},
             "stages_ms": stage_ms, "stage_roofline": stage_frac,

@@ -102,9 +102,9 @@ typedef struct {
   float* pose;     /* [n_views, 6]: dL/d(rho_xyz, phi_xyz) */
 } splat2d_grads;
 
-/* Rasterizer constants.  Defaults (splat2d_default_config): 16x16 tiles,
- * chunk 256, alpha in [1/255, 0.99], t_min 1e-4, lowpass sqrt(1/2) px,
- * z_near 0.01, black background. */
+/* Rasterizer constants.  Defaults (splat2d_default_config): 8x8 tiles,
+ * chunk 128 (forward) and 64 (backward), alpha in [1/255, 0.99], t_min 1e-4,
+ * lowpass sqrt(1/2) px, z_near 0.01, black background. */
 typedef struct {
   int32_t tile_w, tile_h;   /* one of 8x8, 16x16, 32x8 */
   int32_t chunk;            /* surfels staged per shared-memory batch: 64, 128, 256 (or 512 with 256-pixel tiles) */
@@ -115,6 +115,7 @@ typedef struct {
   float z_near;             /* cull surfels whose opacity-aware disk reaches z <= z_near */
   float bg[3];              /* background colour added as T_final * bg */
   uint32_t flags;           /* SPLAT2D_FLAG_* */
+  int32_t bwd_chunk;        /* chunk of the backward compositing pass (0 = chunk; same values as chunk) */
 } splat2d_config;
 
 /* flags */

@@ -40,7 +40,7 @@ class Grads(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("chunk", c_int32), ("alpha_min", c_float),
                 ("alpha_max", c_float), ("t_min", c_float), ("lowpass_sigma", c_float), ("z_near", c_float),
-                ("bg", c_float * 3), ("flags", c_uint32)]
+                ("bg", c_float * 3), ("flags", c_uint32), ("bwd_chunk", c_int32)]
 
 
 class Problem(ctypes.Structure):

@@ -37,8 +37,10 @@ static bool valid_config(const splat2d_config* c) {
   if (!c) return false;
   const bool tile_ok = (c->tile_w == 16 && c->tile_h == 16) || (c->tile_w == 8 && c->tile_h == 8) ||
                        (c->tile_w == 32 && c->tile_h == 8);
-  const bool chunk_ok = c->chunk == 64 || c->chunk == 128 || c->chunk == 256 ||
-                        (c->chunk == 512 && c->tile_w * c->tile_h == 256);
+  auto chunk_valid = [&](int ch) {
+    return ch == 64 || ch == 128 || ch == 256 || (ch == 512 && c->tile_w * c->tile_h == 256);
+  };
+  const bool chunk_ok = chunk_valid(c->chunk) && (c->bwd_chunk == 0 || chunk_valid(c->bwd_chunk));
   if (!tile_ok || !chunk_ok) return false;
   if (!(c->alpha_min > 0.f && c->alpha_min < 1.f)) return false;
   if (!(c->alpha_max >= c->alpha_min && c->alpha_max < 1.f)) return false;
@@ -210,9 +212,10 @@ extern "C" {
 void splat2d_default_config(splat2d_config* c) {
   if (!c) return;
   std::memset(c, 0, sizeof(*c));
-  c->tile_w = 16;
-  c->tile_h = 16;
-  c->chunk = 256;
+  c->tile_w = 8;
+  c->tile_h = 8;
+  c->chunk = 128;
+  c->bwd_chunk = 64;
   c->alpha_min = 1.0f / 255.0f;
   c->alpha_max = 0.99f;
   c->t_min = 1e-4f;
@@ -304,7 +307,7 @@ int splat2d_render_bwd_tiles(const splat2d_config* cfg, const splat2d_problem* p
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
-  if (launch_render_bwd(L, make_params(cfg), cfg->chunk, w, vals, d_rgb, d_depth, d_normal, d_alpha, st) !=
+  if (launch_render_bwd(L, make_params(cfg), cfg->bwd_chunk ? cfg->bwd_chunk : cfg->chunk, w, vals, d_rgb, d_depth, d_normal, d_alpha, st) !=
       cudaSuccess)
     return SPLAT2D_ERR_CUDA;
   return SPLAT2D_OK;

@@ -75,18 +75,24 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
     }
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
     for (uint32_t k = 0; k < kmax; k++) {
+      // neighbouring records (neighbouring pixels of a keyframe) mostly hit
+      // the same tile at the same k: lanes aggregate runs of equal tiles
       const bool has = k < nt;
       const uint32_t t = has ? (uint32_t)(tbase + (ty0 + (int)k / w) * tilesx + tx0 + (int)k % w) : 0xffffffffu;
-      const uint32_t peers = __match_any_sync(0xffffffffu, t);
-      if (!has) continue;
-      const int leader = __ffs(peers) - 1;
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1);
+      const uint32_t next = __shfl_down_sync(0xffffffffu, t, 1);
+      const uint32_t heads = __ballot_sync(0xffffffffu, has && (lane == 0 || prev != t));
+      const uint32_t ends = __ballot_sync(0xffffffffu, has && (lane == 31 || next != t));
+      const int leader = 31 - __clz(heads & (lt_mask | (1u << lane)));  // run start at or below this lane
+      const bool lead = has && leader == lane;
+      const uint32_t run = lead ? (uint32_t)(__ffs(ends & ~lt_mask) - lane) : 0u;
       if (!SCATTER) {
-        if (lane == leader) atomicAdd(A.counts + t, (uint32_t)__popc(peers));
+        if (lead) atomicAdd(A.counts + t, run);
       } else {
         uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(A.counts + t, (uint32_t)__popc(peers));
-        base = __shfl_sync(peers, base, leader);
-        A.bucket[base + __popc(peers & lt_mask)] = comp;
+        if (lead) base = atomicAdd(A.counts + t, run);
+        base = __shfl_sync(0xffffffffu, base, leader & 31);
+        if (has) A.bucket[base + (uint32_t)(lane - leader)] = comp;
       }
     }
   }

@@ -16,9 +16,10 @@
 // tile stops staging as soon as all its pixels have stopped.
 // Backward: back to front per pixel from its last blended entry, T recovered
 // by division, one scalar suffix sum per pixel (the upstream gradient dotted
-// with the features of the entries behind); each lane adds its pair's
-// gradient to the entry's shared-memory slot, and after the chunk one set of
-// vector atomics per (tile, entry) moves the sums to the gradient record.
+// with the features of the entries behind), evaluated 32 (pixel, entry) pairs
+// at a time with segmented warp scans; each lane adds its pair's gradient to
+// the entry's shared-memory slot, and after the chunk one set of vector
+// atomics per (tile, entry) moves the sums to the gradient record.
 #include <cuda_runtime.h>
 
 #include "splat2d_internal.cuh"
@@ -148,6 +149,23 @@ __device__ __forceinline__ uint32_t lane_word(const SRecs<CHUNK>& s_rec, int wd,
 #pragma unroll
   for (int r = 1; r < 4; r++) rw = (mr == r) ? rowb[r] : rw;
   return cw & rw;
+}
+
+// Position of the r-th set bit (r >= 1, counted from bit 0) of a word that
+// has at least r set bits: a binary search on population counts of halves.
+__device__ __forceinline__ int nth_set_bit(uint32_t b, int r) {
+  int pos = 0, c;
+  c = __popc(b & 0xffffu);
+  if (r > c) { r -= c; b >>= 16; pos += 16; }
+  c = __popc(b & 0xffu);
+  if (r > c) { r -= c; b >>= 8; pos += 8; }
+  c = __popc(b & 0xfu);
+  if (r > c) { r -= c; b >>= 4; pos += 4; }
+  c = __popc(b & 0x3u);
+  if (r > c) { r -= c; b >>= 2; pos += 2; }
+  c = (int)(b & 1u);
+  if (r > c) pos += 1;
+  return pos;
 }
 
 // Sum 8 per-lane values over the warp and give every lane all 8 totals
@@ -454,43 +472,56 @@ __device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const
   }
 }
 
-// Dynamic shared memory of the backward kernel.
+// Dynamic shared memory of the backward kernel (per-pixel arrays indexed by
+// the pixel's slot, see k_render_bwd).
 template <int NT, int CHUNK>
 struct BwdSmem {
-  static constexpr int RING = 2 * CHUNK;  // >= CHUNK + 32, a power of two
   SRecs<CHUNK> rec;
   float grad[CHUNK * SGRAD_STRIDE];
   uint32_t idx[CHUNK];
   uint32_t pbits[NT][CHUNK / 32];  // per pixel: chunk entries whose rect holds it, below its last
+  uint16_t pcnt[NT][CHUNK / 32];   // per pixel: set bits in its mask words >= w (from the deepest word)
   float4 up[NT][2];                // per pixel: dC0 dC1 dC2 dD | dN0 dN1 dN2 dA*T_final
   float2 tq[NT];                   // per pixel: (T in front of the deepest unprocessed entry, Q behind it)
-  uint32_t ring[NT / 32][RING];    // per warp: queued (pixel << 16 | entry), deepest entry first per pixel
-  uint16_t apix[NT];
-  int item, nact, next;
+  uint8_t own[NT / 32][32];        // per warp and step: lane of the pixel whose run starts at each position
+  int item;
   uint32_t top;
 };
 
 // The reverse pass streams (pixel, entry) pairs.  Per chunk, each warp
-// builds its 8x4 patch's per-pixel entry masks with ballots; then the warps
-// pull the tile's pixels that still have entries in the chunk and queue each
-// pixel's entries, deepest first, in a per-warp ring.  Every step takes the
-// next 32 queued pairs -- usually several pixels -- and evaluates them in
-// parallel: within each pixel's run (segments found with a ballot of run
-// starts), a segmented prefix product of 1/(1 - alpha) recovers the
-// transmittance in front of each entry and a segmented prefix sum gives the
-// sum behind it; every lane then adds its own pair's gradient terms to the
-// entry's shared-memory slot, and the last lane of each run stores the
-// pixel's running (T, Q) for its next run.
+// builds its 8x4 patch's per-pixel entry masks with ballots.  Then each warp
+// takes 32 pixels spread over the tile (a diagonal interleave, so the warps'
+// loads match), one per lane, and lays their pairs end to end -- pixel by pixel,
+// each pixel's entries deepest first -- at offsets given by a warp prefix sum
+// of the mask population counts.  Every step takes the next 32 positions of
+// that stream: a lane finds its pixel from the OR-reduced mask of the run
+// starts in the step and its entry by selecting a set bit of the pixel's
+// mask, so the stream is never materialised.  Within each pixel's run a
+// segmented prefix product of 1/(1 - alpha) recovers the transmittance in
+// front of each entry and a segmented prefix sum gives the sum behind it;
+// every lane adds its own pair's gradient terms to the entry's shared-memory
+// slot, and the last lane of each run stores the pixel's running (T, Q) for
+// its next run.
 template <int TW, int TH, int CHUNK>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 8) : 2) k_render_bwd(const RenderArgs A) {
   constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
-  constexpr int RING = BwdSmem<NT, CHUNK>::RING;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BwdSmem<NT, CHUNK>& S = *reinterpret_cast<BwdSmem<NT, CHUNK>*>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t le_mask = (2u << lane) - 1u;  // lanes <= this lane
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
-  uint32_t* ring = S.ring[wid];
+  uint8_t* own = S.own[wid];
+  // The pixel at tile-local (x, y) is laid out by warp (x + 3y) mod NW -- a
+  // diagonal interleave, so every warp's 32 pixels spread over the whole tile
+  // and the warps' loads match -- as that warp's pixel number
+  // y * (TW / NW) + x / NW.  Per-pixel shared arrays are indexed by slot =
+  // warp * 32 + number, so one warp's pixels sit in consecutive slots.
+  constexpr int PR = TW / NW;  // pixels per row of one warp
+  static_assert(TW % NW == 0 && PR * TH == 32, "each warp lays out 32 pixels");
+  const int lx = (wid % WX) * 8 + (lane & 7), ly = (wid / WX) * 4 + (lane >> 3);
+  const int myslot = ((lx + 3 * ly) % NW) * 32 + ly * PR + lx / NW;  // slot of this thread's own pixel
+  const int mine = wid * 32 + lane;                                  // slot of the pixel this lane lays out
   for (int i = threadIdx.x; i < CHUNK * SGRAD_STRIDE; i += NT) S.grad[i] = 0.f;
   for (;;) {
     if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_bwd, 1u);
@@ -527,8 +558,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         if (A.d_alpha) u1.w = A.d_alpha[vw.poff + pix] * T;
         Q = T * (u0.x * P.bg[0] + u0.y * P.bg[1] + u0.z * P.bg[2]);
       }
-      S.up[threadIdx.x][0] = u0;
-      S.up[threadIdx.x][1] = u1;
+      S.up[myslot][0] = u0;
+      S.up[myslot][1] = u1;
     }
     if (threadIdx.x == 0) S.top = range.x;
     __syncthreads();
@@ -540,75 +571,85 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int count = (int)(hi - lo);
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
-      if (threadIdx.x == 0) {
-        S.nact = 0;
-        S.next = 0;
-      }
       stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx);
       __syncthreads();
       // per-pixel masks of this chunk, restricted to the entries below the pixel's last
       const int lim = act ? (int)min64((int64_t)my_last - lo, count) : 0;
-      for (int wd = 0; wd < nwd; wd++) {
-        uint32_t m = lane_word(S.rec, wd, count, bx, by, lane);
-        const int keep = lim - wd * 32;
-        m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
-        S.pbits[threadIdx.x][wd] = m;
-      }
-      if (act) {
-        const int k = atomicAdd(&S.nact, 1);
-        S.apix[k] = (uint16_t)threadIdx.x;
-        S.tq[threadIdx.x] = make_float2(T, Q);
-      }
-      __syncthreads();
-      const int n_act = S.nact;
-      int head = 0, pending = 0;
-      bool more = true;
-      for (;;) {
-        // queue pixels until a full step is pending
-        while (pending < 32 && more) {
-          int k = 0;
-          if (lane == 0) k = atomicAdd(&S.next, 1);
-          k = __shfl_sync(0xffffffffu, k, 0);
-          if (k >= n_act) {
-            more = false;
-            break;
+      {
+        int pc[NWD];
+#pragma unroll
+        for (int wd = 0; wd < NWD; wd++) {
+          uint32_t m = 0;
+          if (wd < nwd) {
+            m = lane_word(S.rec, wd, count, bx, by, lane);
+            const int keep = lim - wd * 32;
+            m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
+            S.pbits[myslot][wd] = m;
           }
-          const uint32_t pth = S.apix[k];
-          for (int wd = nwd - 1; wd >= 0; wd--) {
-            const uint32_t bits = S.pbits[pth][wd];
-            if (!bits) continue;
-            if ((bits >> lane) & 1u) {
-              const int above = __popc(bits & ~((2u << lane) - 1u));  // deeper entries of this word
-              ring[(head + pending + above) & (RING - 1)] = (pth << 16) | (uint32_t)(wd * 32 + lane);
-            }
-            pending += __popc(bits);
-          }
-          __syncwarp();
+          pc[wd] = __popc(m);
         }
-        if (pending == 0) break;
-        const int nstep = min(32, pending);
-        const bool has = lane < nstep;
-        const uint32_t pr = has ? ring[(head + lane) & (RING - 1)] : 0xffffffffu;
-        const uint32_t pth = pr >> 16;
-        const int j = (int)(pr & 0xffffu);
-        // runs of one pixel: starts and ends within this step
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, pr, 1);
-        const uint32_t nextp = __shfl_down_sync(0xffffffffu, pr, 1);
-        const bool start = has && (lane == 0 || (prev >> 16) != pth);
-        const bool end = has && (lane == nstep - 1 || (nextp >> 16) != pth);
+        int acc = 0;
+#pragma unroll
+        for (int wd = NWD - 1; wd >= 0; wd--) {
+          acc += pc[wd];
+          S.pcnt[myslot][wd] = (uint16_t)acc;
+        }
+      }
+      if (act) S.tq[myslot] = make_float2(T, Q);
+      __syncthreads();
+      // this warp's stream: its pixels' pairs end to end
+      const uint32_t cnt = S.pcnt[mine][0];
+      uint32_t incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t myoff = incl - cnt;
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      int carry = 0;  // lane of the pixel whose run reaches the previous step's last position
+      for (uint32_t base = 0; base < total; base += 32) {
+        const bool starts_here = cnt > 0 && myoff >= base && myoff < base + 32;
+        if (starts_here) own[myoff - base] = (uint8_t)lane;
+        const uint32_t M = __reduce_or_sync(0xffffffffu, starts_here ? (1u << (myoff - base)) : 0u);
+        __syncwarp();
+        const bool has = base + lane < total;
+        const uint32_t below = M & le_mask;
+        const int ol = below ? (int)own[31 - __clz(below)] : carry;
+        carry = __shfl_sync(0xffffffffu, ol, 31);
+        const uint32_t ooff = __shfl_sync(0xffffffffu, myoff, ol);
+        const int ps = wid * 32 + ol;  // the pixel's slot
+        int j = 0;
+        if (has) {
+          // entry: the q-th set bit of the pixel's mask counted from the
+          // deepest; its word is the last w with pcnt[w] > q
+          const int q = (int)(base + lane - ooff);
+          const uint32_t* pw32 = reinterpret_cast<const uint32_t*>(S.pcnt[ps]);
+          int wd = -1, cin = 0;
+#pragma unroll
+          for (int h = 0; h < NWD / 2; h++) {
+            const uint32_t two = pw32[h];
+            const int c0 = (int)(two & 0xffffu), c1 = (int)(two >> 16);
+            if (c0 > q) { wd = 2 * h; cin = c0; }
+            if (c1 > q) { wd = 2 * h + 1; cin = c1; }
+          }
+          j = wd * 32 + nth_set_bit(S.pbits[ps][wd], cin - q);
+        }
+        const bool start = has && (lane == 0 || ((M >> lane) & 1u));
+        const bool end = has && (lane == 31 || base + lane + 1 == total || ((M >> (lane + 1)) & 1u));
         const uint32_t starts = __ballot_sync(0xffffffffu, start);
-        const int s0 = 31 - __clz(starts & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u)));
+        const int s0 = 31 - __clz(starts & le_mask);
         float2 tq = make_float2(1.f, 0.f);
         float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
         Pair e;
         float alpha = 0.f;
         if (has) {
-          tq = S.tq[pth];
-          u0 = S.up[pth][0];
-          u1 = S.up[pth][1];
-          const int pw = (int)pth >> 5, pl = (int)pth & 31;
-          const float fx = (float)(tx0 + (pw % WX) * 8 + (pl & 7)) + 0.5f;
-          const float fy = (float)(ty0 + (pw / WX) * 4 + (pl >> 3)) + 0.5f;
+          tq = S.tq[ps];
+          u0 = S.up[ps][0];
+          u1 = S.up[ps][1];
+          const int qy = ol / PR, qx = ((wid - 3 * qy) % NW + NW) % NW + (ol % PR) * NW;
+          const float fx = (float)(tx0 + qx) + 0.5f;
+          const float fy = (float)(ty0 + qy) + 0.5f;
           eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], fx, fy, P.lp_scale, P.alpha_max, e);
           alpha = e.alpha;
         }
@@ -652,14 +693,12 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           if (gz != 0.f) atomicAdd(sg + 16, gz);
         }
         __syncwarp();
-        if (end) S.tq[pth] = make_float2(Tb, tq.y + sum);
+        if (end) S.tq[ps] = make_float2(Tb, tq.y + sum);
         __syncwarp();
-        head = (head + nstep) & (RING - 1);
-        pending -= nstep;
       }
       __syncthreads();
       if (act) {
-        const float2 tq = S.tq[threadIdx.x];
+        const float2 tq = S.tq[myslot];
         T = tq.x;
         Q = tq.y;
       }

@@ -24,9 +24,9 @@ __all__ = ["RasterConfig", "Rasterizer", "Images", "SurfelGrads", "Splat2DRender
 class RasterConfig:
     """Constants of the rasterizer (see splat2d_config in include/splat2d.h)."""
 
-    tile_w: int = 16
-    tile_h: int = 16
-    chunk: int = 256
+    tile_w: int = 8
+    tile_h: int = 8
+    chunk: int = 128
     alpha_min: float = 1.0 / 255.0
     alpha_max: float = 0.99
     t_min: float = 1e-4
@@ -35,6 +35,7 @@ class RasterConfig:
     bg: tuple = (0.0, 0.0, 0.0)
     stats: bool = True
     fwd_tail: int = 0  # 0: default; 255: forward always shares pixels across warps
+    bwd_chunk: int = 64  # 0: same as chunk
 
     def to_c(self) -> _abi.Config:
         c = _abi.Config()
@@ -44,6 +45,7 @@ class RasterConfig:
         for i in range(3):
             c.bg[i] = float(self.bg[i])
         c.flags = (0 if self.stats else _abi.FLAG_NO_STATS) | ((int(self.fwd_tail) & 0xFF) << 8)
+        c.bwd_chunk = int(self.bwd_chunk)
         return c
 
 

@@ -52,7 +52,7 @@ def test_workspace_size_and_argument_checks():
     lib = _abi.load()
     cfg = _abi.Config()
     lib.splat2d_default_config(ctypes.byref(cfg))
-    assert (cfg.tile_w, cfg.tile_h, cfg.chunk) == (16, 16, 256)
+    assert (cfg.tile_w, cfg.tile_h, cfg.chunk, cfg.bwd_chunk) == (8, 8, 128, 64)
     assert cfg.alpha_max == pytest.approx(0.99) and cfg.t_min == pytest.approx(1e-4)
     sc = scenes.random_scene(n=100, width=40, height=30, f=30.0, seed=0, n_views=2)
     p = _problem(sc.views, sc.n)
@@ -65,6 +65,12 @@ def test_workspace_size_and_argument_checks():
     bad = _abi.Config.from_buffer_copy(cfg)
     bad.chunk = 100
     assert lib.splat2d_workspace_size(ctypes.byref(bad), ctypes.byref(p)) == 0
+    bad = _abi.Config.from_buffer_copy(cfg)
+    bad.bwd_chunk = 512  # 512-entry chunks need 256-pixel tiles
+    assert lib.splat2d_workspace_size(ctypes.byref(bad), ctypes.byref(p)) == 0
+    ok = _abi.Config.from_buffer_copy(cfg)
+    ok.bwd_chunk = 0  # 0: the forward's chunk
+    assert lib.splat2d_workspace_size(ctypes.byref(ok), ctypes.byref(p)) > 0
     p2 = _problem(sc.views, sc.n)
     p2._keep[1].surfel_offset = 50
     p2._keep[1].surfel_count = 60  # beyond n
@@ -87,7 +93,8 @@ def test_layout_offsets_are_aligned_and_inside():
     lay = _abi.Layout()
     assert lib.splat2d_workspace_layout(ctypes.byref(cfg), ctypes.byref(p), ctypes.byref(lay)) == 0
     assert lay.n_records == 3 * 333 and lay.n_pixels == 3 * 50 * 37
-    assert lay.n_tiles == 3 * 4 * 3
+    tx, ty = -(-50 // cfg.tile_w), -(-37 // cfg.tile_h)
+    assert lay.n_tiles == 3 * tx * ty
     for f in ("records", "ntiles", "keys", "vals", "ranges", "tfinal", "last"):
         off = getattr(lay, f)
         assert off % 256 == 0 and off < lay.total, f

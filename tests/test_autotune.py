@@ -9,15 +9,15 @@ def test_tune_picks_fastest_and_caches(tmp_path):
 
     def fake(c):
         calls.append(c)
-        return {(8, 8, 128): 1.5}.get(c, 2.0 + c[2] / 1000)
+        return {(8, 8, 128, 64): 1.5}.get(c, 2.0 + c[2] / 1000)
 
     best, res = autotune.tune(sc.views, sc.n, fake, path=path)
-    assert best == (8, 8, 128)
+    assert best == (8, 8, 128, 64)
     assert len(calls) == len(autotune.CANDIDATES) and len(res) == len(calls)
-    assert autotune.lookup(sc.views, sc.n, path=path) == (8, 8, 128)
+    assert autotune.lookup(sc.views, sc.n, path=path) == (8, 8, 128, 64)
     # cached: no re-timing
     best2, _ = autotune.tune(sc.views, sc.n, lambda c: 1 / 0, path=path)
-    assert best2 == (8, 8, 128)
+    assert best2 == (8, 8, 128, 64)
     # a different bucket is not served from the cache
     big = scenes.random_scene(n=1000, width=640, height=480, f=500.0, seed=0)
     assert autotune.lookup(big.views, big.n, path=path) is None
@@ -29,3 +29,16 @@ def test_bucket_key_separates_image_size_and_density():
     c = scenes.random_scene(n=1000, width=512, height=384, seed=0, with_target=False)
     ka, kb, kc = (autotune.bucket_key(s.views, s.n) for s in (a, b, c))
     assert len({ka, kb, kc}) == 3
+
+
+def test_lookup_reads_three_field_entries_and_shipped_table(tmp_path, monkeypatch):
+    import json
+    sc = scenes.random_scene(n=1000, width=64, height=48, f=50.0, seed=0, n_views=2)
+    key = autotune.bucket_key(sc.views, sc.n)
+    path = tmp_path / "old.json"
+    path.write_text(json.dumps({key: {"best": [16, 16, 128], "ms": {}}}))
+    assert autotune.lookup(sc.views, sc.n, path=str(path)) == (16, 16, 128, 128)
+    empty = str(tmp_path / "none.json")
+    monkeypatch.setitem(autotune.SHIPPED, key, (8, 8, 128, 64))
+    assert autotune.lookup(sc.views, sc.n, path=empty) == (8, 8, 128, 64)
+    assert autotune.lookup(sc.views, sc.n, path=empty, shipped=False) is None
