@@ -100,12 +100,13 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
 
 // Size classes of the per-tile bucket sorts (upper bounds, inclusive; longer
 // buckets go with the last class).
-constexpr int SORT_CLASS_S = 1024;
-constexpr int SORT_CLASS_M = 4096;
-constexpr int SORT_CLASS_L = 12288;
+constexpr int SORT_CLASSES = 4;
+constexpr int SORT_CLASS_BOUND[SORT_CLASSES] = {1024, 4096, 6144, 12288};
 
 __device__ __forceinline__ int sort_class(uint32_t n) {
-  return n == 0 ? -1 : (n <= (uint32_t)SORT_CLASS_S ? 0 : (n <= (uint32_t)SORT_CLASS_M ? 1 : 2));
+  static_assert(SORT_CLASSES == 4, "one comparison per class bound");
+  constexpr uint32_t b0 = SORT_CLASS_BOUND[0], b1 = SORT_CLASS_BOUND[1], b2 = SORT_CLASS_BOUND[2];
+  return n == 0 ? -1 : (n <= b0 ? 0 : (n <= b1 ? 1 : (n <= b2 ? 2 : 3)));
 }
 
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ count
     // append the tile to its size class's list (order within a list is free)
     const int cls = (i < T && fits) ? sort_class((uint32_t)v) : -1;
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
+    for (int c = 0; c < SORT_CLASSES; c++) {
       const uint32_t m = __ballot_sync(0xffffffffu, cls == c);
       if (!m) continue;
       uint32_t at = 0;
@@ -605,11 +606,11 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 16);
   k_tile_pass<false><<<grid, 256, 0, st>>>(A);
   count_launches(1);
-  uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // 3 queues, 3 list sizes
+  uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // per class: queue, list size
   uint32_t* class_list = reinterpret_cast<uint32_t*>(ws + L.tile_class);
-  e = cudaMemsetAsync(queues, 0, 6 * sizeof(uint32_t), st);
+  e = cudaMemsetAsync(queues, 0, 2 * SORT_CLASSES * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  k_tile_scan<<<1, 1024, 0, st>>>(counts, ranges, L.T, hdr, L.cap, class_list, queues + 3);
+  k_tile_scan<<<1, 1024, 0, st>>>(counts, ranges, L.T, hdr, L.cap, class_list, queues + SORT_CLASSES);
   count_launches(1);
   k_tile_pass<true><<<grid, 256, 0, st>>>(A);
   count_launches(1);
@@ -620,14 +621,19 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   S.keys = reinterpret_cast<uint64_t*>(ws + L.keys0);
   S.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
   S.hdr = hdr;
-  static_assert(SegClass<8, 4>::CAP == SORT_CLASS_S && SegClass<16, 8>::CAP == SORT_CLASS_M &&
-                    SegClass<32, 12>::CAP == SORT_CLASS_L, "class capacities match the class bounds");
-  for (int c = 0; c < 3; c++) {
+  static_assert(SegClass<8, 4>::CAP == SORT_CLASS_BOUND[0] && SegClass<16, 8>::CAP == SORT_CLASS_BOUND[1] &&
+                    SegClass<16, 12>::CAP == SORT_CLASS_BOUND[2] && SegClass<32, 12>::CAP == SORT_CLASS_BOUND[3],
+                "class capacities match the class bounds");
+  for (int c = 0; c < SORT_CLASSES; c++) {
     S.list = class_list + (size_t)c * L.T;
-    S.list_count = queues + 3 + c;
+    S.list_count = queues + SORT_CLASSES + c;
     S.queue = queues + c;
-    e = c == 0 ? launch_tile_sort_class<8, 4, false>(S, st)
-               : (c == 1 ? launch_tile_sort_class<16, 8, false>(S, st) : launch_tile_sort_class<32, 12, true>(S, st));
+    switch (c) {
+      case 0: e = launch_tile_sort_class<8, 4, false>(S, st); break;
+      case 1: e = launch_tile_sort_class<16, 8, false>(S, st); break;
+      case 2: e = launch_tile_sort_class<16, 12, false>(S, st); break;
+      default: e = launch_tile_sort_class<32, 12, true>(S, st); break;
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();

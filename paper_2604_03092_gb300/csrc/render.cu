@@ -238,7 +238,7 @@ struct FwdSmem {
 // warp are still compositing, all warps share them, one pixel at a time.
 
 template <int TW, int TH, int CHUNK>
-__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd(const RenderArgs A) {
+__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd(const RenderArgs A) {
   constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FwdSmem<NT, CHUNK>& S = *reinterpret_cast<FwdSmem<NT, CHUNK>*>(smem_raw);
@@ -434,12 +434,12 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 10 : 3) k_render_fwd
 constexpr int SGRAD_STRIDE = 17;
 
 // Gradient of one kept (pixel, entry) pair w.r.t. the 16 stored record
-// quantities (G_* order) and the depth; `da` is dL/dalpha.
+// quantities (G_* order) and the depth; `da` is dL/dalpha.  Written without
+// branches (selects only): the clamped and the low-pass cases zero the terms
+// they do not carry.
 __device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const float4 qq, float da, float w,
                                            float dC0, float dC1, float dC2, float dD, float dN0, float dN1,
                                            float dN2, float lp_scale, float (&g)[16], float& gz) {
-#pragma unroll
-  for (int k = 0; k < 16; k++) g[k] = 0.f;
   g[G_R] = w * dC0;
   g[G_G] = w * dC1;
   g[G_B] = w * dC2;
@@ -447,29 +447,26 @@ __device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const
   g[G_NX] = w * dN0;
   g[G_NY] = w * dN1;
   g[G_NZ] = w * dN2;
-  if (!e.clamped) {
-    g[G_OP] = da * e.G;
-    const float drho = -kLn2 * e.G * (da * qq.w);
-    float ddx, ddy;
-    if (e.obj) {
-      const float t2 = 2.f * drho * e.rc * e.rc;
-      const float gA = t2 * e.a, gB = t2 * e.b, gC = -2.f * drho * e.rho * e.rc;
-      g[G_P00] = gA * e.dx;
-      g[G_P01] = gA * e.dy;
-      g[G_P10] = gB * e.dx;
-      g[G_P11] = gB * e.dy;
-      g[G_P20] = gC * e.dx;
-      g[G_P21] = gC * e.dy;
-      g[G_P22] = gC;
-      ddx = gA * pp.x + gB * pp.z + gC * qq.x;
-      ddy = gA * pp.y + gB * pp.w + gC * qq.y;
-    } else {
-      ddx = 2.f * lp_scale * e.dx * drho;
-      ddy = 2.f * lp_scale * e.dy * drho;
-    }
-    g[G_CX] = -ddx;
-    g[G_CY] = -ddy;
-  }
+  const float dal = e.clamped ? 0.f : da;  // alpha = alpha_max carries no geometry gradient
+  g[G_OP] = dal * e.G;
+  const float drho = -kLn2 * e.G * (dal * qq.w);
+  // object-space branch (rho = (a^2 + b^2) / c^2); its terms are selected away
+  // when the low-pass term decides (there c may be 0 and rc infinite)
+  const float t2 = 2.f * drho * e.rc * e.rc;
+  const float gA = e.obj ? t2 * e.a : 0.f, gB = e.obj ? t2 * e.b : 0.f;
+  const float gC = e.obj ? -2.f * drho * e.rho * e.rc : 0.f;
+  g[G_P00] = gA * e.dx;
+  g[G_P01] = gA * e.dy;
+  g[G_P10] = gB * e.dx;
+  g[G_P11] = gB * e.dy;
+  g[G_P20] = gC * e.dx;
+  g[G_P21] = gC * e.dy;
+  g[G_P22] = gC;
+  const float lp2 = 2.f * lp_scale * drho;
+  const float ddx = e.obj ? gA * pp.x + gB * pp.z + gC * qq.x : lp2 * e.dx;
+  const float ddy = e.obj ? gA * pp.y + gB * pp.w + gC * qq.y : lp2 * e.dy;
+  g[G_CX] = -ddx;
+  g[G_CY] = -ddy;
 }
 
 // Dynamic shared memory of the backward kernel (per-pixel arrays indexed by
@@ -639,20 +636,15 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         const bool end = has && (lane == 31 || base + lane + 1 == total || ((M >> (lane + 1)) & 1u));
         const uint32_t starts = __ballot_sync(0xffffffffu, start);
         const int s0 = 31 - __clz(starts & le_mask);
-        float2 tq = make_float2(1.f, 0.f);
-        float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
+        // lanes past the stream's end (last step only) evaluate a valid
+        // dummy pair and are masked out by `kept`
+        const float2 tq = S.tq[ps];
+        const float4 u0 = S.up[ps][0], u1 = S.up[ps][1];
+        const int qy = ol / PR, qx = ((wid - 3 * qy) % NW + NW) % NW + (ol % PR) * NW;
         Pair e;
-        float alpha = 0.f;
-        if (has) {
-          tq = S.tq[ps];
-          u0 = S.up[ps][0];
-          u1 = S.up[ps][1];
-          const int qy = ol / PR, qx = ((wid - 3 * qy) % NW + NW) % NW + (ol % PR) * NW;
-          const float fx = (float)(tx0 + qx) + 0.5f;
-          const float fy = (float)(ty0 + qy) + 0.5f;
-          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], fx, fy, P.lp_scale, P.alpha_max, e);
-          alpha = e.alpha;
-        }
+        eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], (float)(tx0 + qx) + 0.5f, (float)(ty0 + qy) + 0.5f, P.lp_scale,
+                  P.alpha_max, e);
+        const float alpha = e.alpha;
         const bool kept = has && alpha >= P.alpha_min;
         const float iom = kept ? rcp_approx(__fsub_rn(1.f, alpha)) : 1.f;
         // segmented prefix product: transmittance in front of this entry
@@ -660,32 +652,30 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const float y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane - o >= s0) x = __fmul_rn(x, y);
+          x = (lane - o >= s0) ? __fmul_rn(x, y) : x;
         }
         const float Tb = tq.x * x;
         const float w = kept ? alpha * Tb : 0.f;
-        float f = 0.f;
-        if (kept) {
-          const float4 col = S.rec.col[j], nrm = S.rec.n[j];
-          f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, fmaf(u0.w, col.w,
-              fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, u1.z * nrm.z))))));
-        }
+        const float4 col = S.rec.col[j], nrm = S.rec.n[j];
+        const float f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, fmaf(u0.w, col.w,
+                        fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, u1.z * nrm.z))))));
         const float wf = w * f;
         // segmented prefix sum: the sum over entries behind this one
         float sum = wf;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const float y = __shfl_up_sync(0xffffffffu, sum, o);
-          if (lane - o >= s0) sum += y;
+          sum = (lane - o >= s0) ? sum + y : sum;
         }
         const float Qb = tq.y + (sum - wf);
         n_eval += has ? 1u : 0u;
+        n_blend += kept ? 1u : 0u;
+        const float da = Tb * f - (Qb - u1.w) * iom;
+        float g[16];
+        float gz;
+        pair_grads(e, S.rec.p[j], S.rec.q[j], da, w, u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, P.lp_scale, g, gz);
         if (kept) {
-          n_blend++;
-          const float da = Tb * f - (Qb - u1.w) * iom;
-          float g[16];
-          float gz;
-          pair_grads(e, S.rec.p[j], S.rec.q[j], da, w, u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, P.lp_scale, g, gz);
+          // zero terms (clamped alpha, low-pass pairs) skip their atomic
           float* sg = S.grad + j * SGRAD_STRIDE;
 #pragma unroll
           for (int q = 0; q < 16; q++)

@@ -104,8 +104,8 @@ def test_preprocess_matches_oracle(seed):
     nrm = rec[:, [14, 15, 16]]
     assert np.abs(nrm[both] - p.rec[both, 12:15]).max() < 1e-6
     # tile counts follow from the pixel rect
-    tx = grect[:, 2] // 16 - grect[:, 0] // 16 + 1
-    ty = grect[:, 3] // 16 - grect[:, 1] // 16 + 1
+    tx = grect[:, 2] // cfg.tile_w - grect[:, 0] // cfg.tile_w + 1
+    ty = grect[:, 3] // cfg.tile_h - grect[:, 1] // cfg.tile_h + 1
     assert np.array_equal(nt[vis_g], (tx * ty)[vis_g])
 
 
@@ -309,10 +309,11 @@ def test_backward_random_scene(seed):
     _check_backward(sc, RasterConfig(bg=(0.3, 0.1, 0.2)), seed=seed)
 
 
-@pytest.mark.parametrize("tile,chunk", [((8, 8), 64), ((32, 8), 128)])
-def test_backward_tile_shapes(tile, chunk):
+@pytest.mark.parametrize("tile,chunk,bwd_chunk", [((8, 8), 64, 64), ((8, 8), 128, 128), ((32, 8), 128, 0),
+                                                   ((16, 16), 256, 512), ((16, 16), 128, 256)])
+def test_backward_tile_shapes(tile, chunk, bwd_chunk):
     sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=3, n_views=2)
-    _check_backward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], chunk=chunk))
+    _check_backward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], chunk=chunk, bwd_chunk=bwd_chunk))
 
 
 def test_backward_keyframe_crop():
