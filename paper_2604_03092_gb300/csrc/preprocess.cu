@@ -317,6 +317,7 @@ struct PreBwdArgs {
   float4* rgrad;  // consumed and cleared: zero again when this kernel ends
   splat2d_grads out;
   int32_t atomic_params;
+  const Header* hdr;
 };
 
 constexpr int kPoseSlots = 64;  // per-block pose accumulators (views)
@@ -324,6 +325,8 @@ constexpr int kPoseSlots = 64;  // per-block pose accumulators (views)
 __global__ void __launch_bounds__(256) k_preprocess_bwd(const PreBwdArgs A) {
   __shared__ float s_pose[kPoseSlots][6];
   __shared__ int s_vfirst;
+  // a failed binning (instance capacity exceeded): nothing was accumulated
+  if (A.hdr->status != 0) return;
   const int64_t wlo = (int64_t)blockIdx.x * A.per_block;
   const int64_t whi = min(wlo + A.per_block, A.n_work);
   if (wlo >= whi) return;
@@ -525,6 +528,7 @@ cudaError_t launch_preprocess_bwd(const splat2d_surfels* S, const Layout& L, con
   A.P = P;
   A.ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
   A.rgrad = reinterpret_cast<float4*>(ws + L.rgrad);
+  A.hdr = reinterpret_cast<const Header*>(ws + L.header);
   A.out = *G;
   A.atomic_params = atomic_params ? 1 : 0;
   int64_t blocks_cap = (int64_t)sm_count() * 8;

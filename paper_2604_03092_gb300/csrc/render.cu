@@ -246,6 +246,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
   const uint32_t lt_mask = (1u << lane) - 1u;
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
+  // a failed binning (instance capacity exceeded) leaves no valid lists
+  if (A.hdr->status != 0) return;
   for (;;) {
     if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_fwd, 1u);
     __syncthreads();
@@ -509,6 +511,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
   uint8_t* own = S.own[wid];
+  // a failed binning (instance capacity exceeded) leaves no valid lists
+  if (A.hdr->status != 0) return;
   // The pixel at tile-local (x, y) is laid out by warp (x + 3y) mod NW -- a
   // diagonal interleave, so every warp's 32 pixels spread over the whole tile
   // and the warps' loads match -- as that warp's pixel number

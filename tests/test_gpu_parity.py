@@ -272,6 +272,32 @@ def test_capacity_overflow_is_reported_and_repaired():
         assert torch.equal(a, b)
 
 
+def test_capacity_overflow_with_surfel_offset_skips_stale_lists():
+    # a view that renders surfels [1500, 3000) of the buffer: after an
+    # overflowed binning the sorted lists are stale (here: zeros, i.e. a
+    # surfel index below the view's range), so the compositing and chain-rule
+    # kernels must not read them; the next checked forward repairs the run
+    sc = scenes.random_scene(n=3000, width=80, height=64, f=60.0, seed=5, n_views=2)
+    sc.views[1].surfel_offset, sc.views[1].surfel_count = 1500, 1500
+    cfg = RasterConfig()
+    params = to_dev(sc)
+    one = Rasterizer([sc.views[1]], sc.n, cfg, capacity=64)
+    out = one.new_images()
+    one.forward(*params, out=out, check=False)
+    grads = one.new_grads()
+    one.render_bwd_tiles((torch.ones(3 * one.n_pixels, device="cuda"), None, None, None))
+    one.preprocess_bwd(*params, grads)
+    assert one.status() == _abi.ERR_CAPACITY
+    for g in grads:
+        assert not torch.any(g)
+    im = one.forward(*params, out=out)
+    assert one.status() == 0
+    batched = Rasterizer(sc.views, sc.n, cfg)
+    imb = batched.forward(*params)
+    for x, y in zip(one.view_images(im, 0), batched.view_images(imb, 1)):
+        assert torch.equal(x, y)
+
+
 # --------------------------------------------------------------------------
 # gradients
 # --------------------------------------------------------------------------
