@@ -28,7 +28,7 @@ _LIB = os.path.join(_LIBDIR, "libsplat2d_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-NREC = 19
+NREC = 20
 ST_VISIBLE, ST_OPACITY, ST_NEAR, ST_EMPTY, ST_INVALID = 0, 1, 2, 3, 4
 SF_TILE_AMBIG, SF_NEAR_AMBIG, SF_PIX_AMBIG = 1, 2, 4
 PF_ALPHA_MIN, PF_T_MIN, PF_RECT, PF_NEAR, PF_ALPHA_MAX, PF_BRANCH = 1, 2, 4, 8, 16, 32
@@ -95,12 +95,16 @@ class Config:
     eps_t: float = 2e-5
     eps_px: float = 2e-5
     eps_z: float = 1e-5
+    # depth output: False = the surfel center's depth (Eq. 1), True = the depth
+    # of the ray-splat intersection where the object-space term decides
+    depth_ray: bool = False
 
     def array(self) -> np.ndarray:
         f32 = lambda x: float(np.float32(x))  # the library receives FP32 constants
         return np.array([f32(self.alpha_min), f32(self.alpha_max), f32(self.t_min), f32(self.sigma_lp),
                          f32(self.z_near), f32(self.bg[0]), f32(self.bg[1]), f32(self.bg[2]),
-                         self.tile_w, self.tile_h, self.eps_alpha, self.eps_t, self.eps_px, self.eps_z],
+                         self.tile_w, self.tile_h, self.eps_alpha, self.eps_t, self.eps_px, self.eps_z,
+                         1.0 if self.depth_ray else 0.0],
                         dtype=np.float64)
 
 
@@ -117,7 +121,7 @@ def _c(a, dt):
 
 @dataclass
 class Prep:
-    rec: np.ndarray       # (n, 19) float64
+    rec: np.ndarray       # (n, 20) float64
     status: np.ndarray    # (n,) int32
     pixrect: np.ndarray   # (n, 4) int32 inclusive x0 y0 x1 y1
     tilerect: np.ndarray  # (n, 4) int32

@@ -23,7 +23,9 @@
  *   alpha_j), and the pixel stops before the first surfel that would take
  *   T below t_min.  Outputs (Eq. 1): I = sum c_i w_i + T_final bg,
  *   D = sum z_i w_i (z_i = depth of mu_c along the optical axis), A = 1 -
- *   T_final, and a camera-frame normal N = sum n_c,i w_i.
+ *   T_final, and a camera-frame normal N = sum n_c,i w_i.  Optionally
+ *   (depth_ray) z_i is taken per pixel as the depth of the ray-splat
+ *   intersection point, where the object-space term decides (2DGS geometry).
  *   For a fronto-parallel surfel this is exactly Eq. 1 with the screen-space
  *   covariance Sigma = (f/z)^2 R2 diag(s^2) R2^T.
  *
@@ -41,10 +43,10 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define NREC 19
+#define NREC 20
 /* record layout (FP64): A = adj(M) row-major (9), projected center (2),
- * depth z, camera normal (3), opacity, rgb (3). */
-enum { R_A = 0, R_CX = 9, R_CY = 10, R_Z = 11, R_N = 12, R_OP = 15, R_RGB = 16 };
+ * depth z, camera normal (3), opacity, rgb (3), det(M). */
+enum { R_A = 0, R_CX = 9, R_CY = 10, R_Z = 11, R_N = 12, R_OP = 15, R_RGB = 16, R_DET = 19 };
 
 /* surfel status */
 enum { ST_VISIBLE = 0, ST_OPACITY = 1, ST_NEAR = 2, ST_EMPTY = 3, ST_INVALID = 4 };
@@ -75,6 +77,7 @@ typedef struct {
   double alpha_min, alpha_max, t_min, sigma_lp, z_near, bg[3];
   int tile_w, tile_h;
   double eps_alpha, eps_t, eps_px, eps_z;
+  int depth_ray;  /* depth output: 0 = z_i of the center, 1 = depth of the ray-splat intersection */
 } cfg_t;
 
 /* cam: W, H, fx, fy, cx, cy, then the 3x4 world-to-camera matrix row-major. */
@@ -93,13 +96,14 @@ static void load_cam(const double* c, cam_t* k) {
 }
 
 /* cfg: alpha_min, alpha_max, t_min, sigma_lp, z_near, bg[3], tile_w, tile_h,
- * eps_alpha, eps_t, eps_px, eps_z. */
+ * eps_alpha, eps_t, eps_px, eps_z, depth_ray. */
 static void load_cfg(const double* c, cfg_t* k) {
   k->alpha_min = c[0]; k->alpha_max = c[1]; k->t_min = c[2];
   k->sigma_lp = c[3]; k->z_near = c[4];
   k->bg[0] = c[5]; k->bg[1] = c[6]; k->bg[2] = c[7];
   k->tile_w = (int)c[8]; k->tile_h = (int)c[9];
   k->eps_alpha = c[10]; k->eps_t = c[11]; k->eps_px = c[12]; k->eps_z = c[13];
+  k->depth_ray = c[14] != 0.0;
 }
 
 /* Rotation matrix of a unit quaternion (w, x, y, z), row-major. */
@@ -249,6 +253,8 @@ int oracle_preprocess(int64_t n, const float* means, const float* scales, const 
     r[R_CX] = g.M[2] / g.M[8];
     r[R_CY] = g.M[5] / g.M[8];
     r[R_Z] = g.mc[2];
+    /* det(M), from M adj(M) = det(M) I */
+    r[R_DET] = g.M[0] * g.A[0] + g.M[1] * g.A[3] + g.M[2] * g.A[6];
     for (int k = 0; k < 3; k++) r[R_N + k] = g.nc[k];
     r[R_OP] = op;
     for (int k = 0; k < 3; k++) r[R_RGB + k] = rgb[3 * s + k];
@@ -335,7 +341,8 @@ int oracle_preprocess(int64_t n, const float* means, const float* scales, const 
 /* One (pixel, surfel) evaluation in FP64. */
 typedef struct {
   double alpha, raw, G, u, v, a, b, c, rho_obj, rho_lp;
-  int obj, clamped;
+  double z;   /* depth the pair contributes to the depth output */
+  int obj, clamped, zray;
 } eval_t;
 
 static void eval_pair(const double* r, double px, double py, const cfg_t* cfg, eval_t* e) {
@@ -359,6 +366,13 @@ static void eval_pair(const double* r, double px, double py, const cfg_t* cfg, e
   e->raw = r[R_OP] * e->G;
   e->clamped = e->raw > cfg->alpha_max;
   e->alpha = e->clamped ? cfg->alpha_max : e->raw;
+  /* Depth of the pair.  Default: the surfel center's depth z_i (Eq. 1).
+   * With depth_ray, where the object-space term decides: the depth of the
+   * point where the pixel's ray meets the surfel plane.  That point is
+   * u U + v V + mu_c with (u, v, 1) = adj(M) x / c, and K times it equals
+   * M (u, v, 1) = det(M) x / c, whose third entry is det(M) / c. */
+  e->zray = cfg->depth_ray && e->obj && e->c != 0;
+  e->z = e->zray ? r[R_DET] / e->c : r[R_Z];
 }
 
 /* Candidate order: ascending (z32 bits, surfel index). */
@@ -501,7 +515,7 @@ static int64_t walk_pixel(const view_t* V, const cfg_t* cfg, int ix, int iy, dou
     if (fabs(e.rho_obj - e.rho_lp) <= 1e-6 * (1.0 + e.rho_lp)) fl |= PF_BRANCH;
     double w = e.alpha * T;
     for (int ch = 0; ch < 3; ch++) C[ch] += w * r[R_RGB + ch];
-    Dd += w * r[R_Z];
+    Dd += w * e.z;
     for (int ch = 0; ch < 3; ch++) N[ch] += w * r[R_N + ch];
     if (out && nb < cap) {
       out[nb].s = s;
@@ -593,7 +607,7 @@ int oracle_render_pixels(int mode, int64_t n, const double* rec, const int32_t* 
 /*
  * Reverse pass of one view.  Upstream gradients g8 are [8][H][W] (same
  * channel order as the outputs).  Record gradients (dL/d of the 19 record
- * fields) are accumulated into grec[n*19]; the chain rule to the surfel
+ * fields) are accumulated into grec[n*20]; the chain rule to the surfel
  * parameters and the camera se(3) tangent is oracle_chain().  Only pixels
  * whose index is listed in pix (or all pixels if npix < 0) contribute.
  */
@@ -643,15 +657,24 @@ int oracle_render_bwd(int mode, int64_t n, const double* rec, const int32_t* sta
           g[R_RGB + c] = w * dC[c];
           da += dC[c] * (Ti * r[R_RGB + c] - SC[c] / om);
         }
-        g[R_Z] = w * dD;
-        da += dD * (Ti * r[R_Z] - SD / om);
+        const double zi = b->e.z;
+        if (b->e.zray) {
+          /* z = det(M) / c with c = A[6] px + A[7] py + A[8] */
+          double dz = w * dD, c = b->e.c;
+          g[R_DET] = dz / c;
+          double x[3] = {px, py, 1.0};
+          for (int j = 0; j < 3; j++) g[R_A + 6 + j] -= dz * zi / c * x[j];
+        } else {
+          g[R_Z] = w * dD;
+        }
+        da += dD * (Ti * zi - SD / om);
         for (int c = 0; c < 3; c++) {
           g[R_N + c] = w * dN[c];
           da += dN[c] * (Ti * r[R_N + c] - SN[c] / om);
         }
         da += dA * tf / om;
         for (int c = 0; c < 3; c++) SC[c] += w * r[R_RGB + c];
-        SD += w * r[R_Z];
+        SD += w * zi;
         for (int c = 0; c < 3; c++) SN[c] += w * r[R_N + c];
         if (!b->e.clamped) {
           g[R_OP] = da * b->e.G;
@@ -665,7 +688,7 @@ int oracle_render_bwd(int mode, int64_t n, const double* rec, const int32_t* sta
             for (int j = 0; j < 3; j++) {
               g[R_A + 0 + j] = dac * x[j];
               g[R_A + 3 + j] = dbc * x[j];
-              g[R_A + 6 + j] = dcc * x[j];
+              g[R_A + 6 + j] += dcc * x[j];
             }
           } else {
             double s2 = cfg.sigma_lp * cfg.sigma_lp;
@@ -711,6 +734,9 @@ int oracle_chain(int64_t n, const float* means, const float* scales, const float
     if (!make_geom(means + 3 * s, scales + 2 * s, quats + 4 * s, &cam, &g)) continue;
     double dM[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     adj3_vjp(g.M, gr + R_A, dM);
+    /* d det(M) / d M_ij = adj(M)_ji */
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 3; j++) dM[i * 3 + j] += gr[R_DET] * g.A[j * 3 + i];
     double m22 = g.M[8];
     dM[2] += gr[R_CX] / m22;
     dM[5] += gr[R_CY] / m22;

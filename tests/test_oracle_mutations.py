@@ -28,6 +28,12 @@ MUTATIONS = [
     ("rect too small", "double lo = fmin(fmin(r1, r2), c0 - rlp)", "double lo = fmin(fmin(r1, r2), c0 - rlp) + 0.3"),
     ("opacity-aware extent", "double k2 = 2.0 * log(op / cfg.alpha_min);", "double k2 = 1.5 * log(op / cfg.alpha_min);"),
     ("homogeneous divide gradient", "dcc = -(b->e.u * du + b->e.v * dv) / c;", "dcc = -(b->e.u * du - b->e.v * dv) / c;"),
+    ("ray depth: divide term of its gradient", "g[R_A + 6 + j] -= dz * zi / c * x[j];",
+     "g[R_A + 6 + j] -= 0.5 * dz * zi / c * x[j];"),
+    ("ray depth: determinant jacobian transposed", "dM[i * 3 + j] += gr[R_DET] * g.A[j * 3 + i];",
+     "dM[i * 3 + j] += gr[R_DET] * g.A[i * 3 + j];"),
+    ("ray depth where the low-pass term decides", "e->zray = cfg->depth_ray && e->obj && e->c != 0;",
+     "e->zray = cfg->depth_ray && e->c != 0;"),
 ]
 
 

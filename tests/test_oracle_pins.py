@@ -164,6 +164,70 @@ def test_tilted_surfel_matches_ray_plane_intersection(seed):
     assert (im.alpha > 0).sum() >= 3
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ray_depth_matches_ray_plane_intersection(seed):
+    """f1: with the per-pixel depth option, a single tilted surfel's depth
+    output divided by its alpha is, at every pixel it covers, the depth of
+    the point where the pixel's ray meets the surfel plane -- found here by
+    the plane equation n . X = n . mu_c (independent of the adjugate and of
+    det(M)); without the option it is the center's depth everywhere."""
+    rng = np.random.default_rng(300 + seed)
+    Rc = Rotation.from_rotvec(rng.normal(size=3) * 0.2).as_matrix()
+    tc = rng.normal(size=3) * 0.3
+    Rt = np.concatenate([Rc, tc[:, None]], 1).astype(np.float32)
+    view = _view(W=36, H=28, f=35.0, Rt=Rt)
+    Rc32, tc32 = Rt[:, :3].astype(np.float64), Rt[:, 3].astype(np.float64)
+    mc = np.array([0.05, -0.05, 2.0]) + rng.normal(size=3) * 0.05
+    mu = Rc32.T @ (mc - tc32)
+    q = rng.normal(size=4)
+    su, sv, sigma = 0.3, 0.02, 0.8  # thin: the screen-space term wins across it near the center
+    m = np.asarray(mu, np.float32).astype(np.float64)
+    Rs = _rot(np.asarray(q, np.float32).astype(np.float64))
+    mcam = Rc32 @ m + tc32
+    s32 = np.asarray([su, sv], np.float32).astype(np.float64)
+    U, V = Rc32 @ Rs[:, 0] * s32[0], Rc32 @ Rs[:, 1] * s32[1]
+    n = np.cross(U, V)
+    jj, ii = np.meshgrid(np.arange(view.height), np.arange(view.width), indexing="ij")
+    dirs = np.stack([(ii + 0.5 - view.cx) / view.fx, (jj + 0.5 - view.cy) / view.fy, np.ones_like(ii, float)], -1)
+    zplane = (n @ mcam) / (dirs @ n)
+    # which term of the low-pass max decides at each pixel (u, v from the plane point)
+    X = dirs * zplane[..., None]
+    Gm = np.array([[U @ U, U @ V], [U @ V, V @ V]])
+    uv = np.stack([(X - mcam) @ U, (X - mcam) @ V], -1) @ np.linalg.inv(Gm).T
+    rho_obj = (uv ** 2).sum(-1)
+    cx, cy = view.fx * mcam[0] / mcam[2] + view.cx, view.fy * mcam[1] / mcam[2] + view.cy
+    rho_lp = ((ii + 0.5 - cx) ** 2 + (jj + 0.5 - cy) ** 2) / 0.5
+    for ray, lp in ((True, 0.0), (False, 0.0), (True, 0.70710678118654752)):
+        cfg = oracle.Config(sigma_lp=lp, depth_ray=ray)
+        im, p = _render(mu, [su, sv], q, sigma, [1, 1, 1], view, cfg)
+        cov = im.alpha > 0
+        assert cov.sum() > 10
+        z = im.depth[cov] / im.alpha[cov]
+        if not ray:
+            np.testing.assert_allclose(z, mcam[2], rtol=1e-12)
+        elif lp == 0.0:
+            np.testing.assert_allclose(z, zplane[cov], rtol=1e-10)
+        else:
+            # with the low-pass max, pixels where the screen-space term wins
+            # take the center's depth (pixels with the two terms within 1e-6
+            # of a tie are not checked)
+            obj = (rho_obj <= rho_lp)[cov]
+            clear = (np.abs(rho_obj - rho_lp) > 1e-6 * (1 + rho_lp))[cov]
+            np.testing.assert_allclose(z[obj & clear], zplane[cov][obj & clear], rtol=1e-10)
+            np.testing.assert_allclose(z[~obj & clear], mcam[2], rtol=1e-12)
+            assert (obj & clear).sum() > 5 and (~obj & clear).sum() > 0
+
+
+def test_ray_depth_fronto_parallel_is_center_depth():
+    """f1: a surfel parallel to the image plane meets every ray at its
+    center's depth, so both depth readings give the same image."""
+    view = _view(W=30, H=24, f=30.0)
+    mu, q = [0.05, -0.02, 2.5], [1.0, 0.0, 0.0, 0.0]
+    ims = [_render(mu, [0.2, 0.12], q, 0.7, [0.2, 0.5, 0.9], view, oracle.Config(depth_ray=r))[0] for r in (0, 1)]
+    np.testing.assert_allclose(ims[1].out, ims[0].out, rtol=1e-12, atol=1e-15)
+    assert (ims[0].alpha > 0).sum() > 20
+
+
 def test_two_surfels_blend_front_to_back():
     """P4: two surfels centred on the same pixel at depths z1 < z2:
     C = c1 s1 + c2 s2 (1 - s1), D = z1 s1 + z2 s2 (1 - s1), regardless of
@@ -356,11 +420,11 @@ def test_bin_sort_is_a_stable_sort_of_the_rect_instances():
 # gradients: FP64 central differences and rigid-motion identities
 # --------------------------------------------------------------------------
 
-def _loss_setup(seed, n=48, W=28, H=22, f=26.0):
+def _loss_setup(seed, n=48, W=28, H=22, f=26.0, depth_ray=False):
     sc = scenes.random_scene(n=n, width=W, height=H, f=f, seed=seed)
     Rc = Rotation.from_rotvec(np.random.default_rng(seed).normal(size=3) * 0.05).as_matrix()
     sc.views[0].Rt = np.concatenate([Rc, np.array([[0.02], [-0.03], [0.1]])], 1).astype(np.float32)
-    cfg = oracle.Config(bg=(0.1, 0.2, 0.3))
+    cfg = oracle.Config(bg=(0.1, 0.2, 0.3), depth_ray=depth_ray)
     g8 = np.random.default_rng(seed + 99).normal(size=(8, H, W))
     return sc, cfg, g8
 
@@ -371,12 +435,13 @@ def _loss(sc, cfg, g8, cam=None):
     return float((g8 * im.out).sum()), im.phash
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_gradient_matches_central_differences(seed):
+@pytest.mark.parametrize("seed,depth_ray", [(0, False), (1, False), (2, True), (3, True)])
+def test_gradient_matches_central_differences(seed, depth_ray):
     """P7: analytic gradient of L = sum(g . outputs) w.r.t. every parameter
     vs FP64 central differences; parameters whose +-h step changes any
-    discrete decision (decision hash) are skipped."""
-    sc, cfg, g8 = _loss_setup(seed)
+    discrete decision (decision hash) are skipped.  Also with the per-pixel
+    ray-splat intersection depth."""
+    sc, cfg, g8 = _loss_setup(seed, depth_ray=depth_ray)
     p = oracle.preprocess_scene_view(sc, 0, cfg)
     g = oracle.render_bwd(sc.means, sc.scales, sc.quats, p, g8)
     checked = 0
@@ -405,11 +470,11 @@ def test_gradient_matches_central_differences(seed):
     assert checked > 300
 
 
-@pytest.mark.parametrize("seed", [0, 1])
-def test_pose_gradient_matches_central_differences(seed):
+@pytest.mark.parametrize("seed,depth_ray", [(0, False), (1, False), (2, True)])
+def test_pose_gradient_matches_central_differences(seed, depth_ray):
     """P7 for the camera: d L / d xi at xi = 0 for T_cw <- Exp(xi) T_cw,
     xi = (rho, phi); FD through rho -> t + rho and phi -> R(phi) [R | t]."""
-    sc, cfg, g8 = _loss_setup(seed)
+    sc, cfg, g8 = _loss_setup(seed, depth_ray=depth_ray)
     p = oracle.preprocess_scene_view(sc, 0, cfg)
     g = oracle.render_bwd(sc.means, sc.scales, sc.quats, p, g8)
     cam0 = oracle.cam_array(sc.views[0])
