@@ -120,6 +120,13 @@ typedef struct {
 
 /* flags */
 #define SPLAT2D_FLAG_NO_STATS 1u   /* skip the pair counters (kept by default) */
+/* Depth output per pixel from the ray-splat intersection: each pair
+ * contributes the depth of the point where the pixel's ray meets the surfel
+ * plane (2D Gaussian Splatting's per-pixel geometry) wherever the
+ * object-space term of the low-pass max decides, and its center's depth
+ * z_i elsewhere.  Default off: z_i of the center for every pair, as Eq. 1
+ * of the paper (Sec. 3) writes it. */
+#define SPLAT2D_FLAG_DEPTH_RAY 2u
 /* Bits 8..15 of flags: forward tail threshold, pixels per warp of a tile below
  * which the forward shares the tile's remaining pixels across all warps
  * (0 = the default of 8; 255 = always).  A launch-shape knob for the

@@ -18,6 +18,7 @@ ERR_CAPACITY = -4
 ERR_TIMEOUT = -5
 ERR_NO_DEVICE = -6
 FLAG_NO_STATS = 1
+FLAG_DEPTH_RAY = 2
 SORT_NOALLOC_MAX_PAIRS = 1 << 20
 
 

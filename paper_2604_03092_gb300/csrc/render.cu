@@ -79,6 +79,16 @@ __device__ __forceinline__ void eval_pair(const float4 c, const float4 p, const 
   e.alpha = e.clamped ? alpha_max : raw;
 }
 
+// Depth a pair contributes to the depth output: the center's depth z
+// (record), or with the ray option, where the object-space term decides, the
+// depth of the ray-splat intersection.  The record's third row is the
+// normalised plane normal: c = N n.d(x) with d(x) the pixel's ray (z = 1),
+// and at the center c = p22 = N n.mu_c / z, so the plane depth n.mu_c / n.d(x)
+// is z p22 / c.
+__device__ __forceinline__ float pair_depth(const Pair& e, float z, float p22, int depth_ray) {
+  return (depth_ray && e.obj) ? z * p22 * e.rc : z;
+}
+
 __device__ __forceinline__ bool in_rect(const int4 r, int px, int py) {
   return (unsigned)(px - r.x) <= (unsigned)r.z && (unsigned)(py - r.y) <= (unsigned)r.w;
 }
@@ -305,7 +315,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
           C0 = __fmaf_rn(w, col.x, C0);
           C1 = __fmaf_rn(w, col.y, C1);
           C2 = __fmaf_rn(w, col.z, C2);
-          D = __fmaf_rn(w, col.w, D);
+          D = __fmaf_rn(w, pair_depth(e, col.w, S.rec.q[j].z, P.depth_ray), D);
           N0 = __fmaf_rn(w, nrm.x, N0);
           N1 = __fmaf_rn(w, nrm.y, N1);
           N2 = __fmaf_rn(w, nrm.z, N2);
@@ -368,7 +378,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
             float vals[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (contrib) {
               const float4 col = S.rec.col[j], nrm = S.rec.n[j];
-              vals[0] = w * col.x; vals[1] = w * col.y; vals[2] = w * col.z; vals[3] = w * col.w;
+              vals[0] = w * col.x; vals[1] = w * col.y; vals[2] = w * col.z;
+              vals[3] = w * pair_depth(e, col.w, S.rec.q[j].z, P.depth_ray);
               vals[4] = w * nrm.x; vals[5] = w * nrm.y; vals[6] = w * nrm.z;
             }
             warp_sum8_all(vals, lane);
@@ -469,6 +480,23 @@ __device__ __forceinline__ void pair_grads(const Pair& e, const float4 pp, const
   const float ddy = e.obj ? gA * pp.y + gB * pp.w + gC * qq.y : lp2 * e.dy;
   g[G_CX] = -ddx;
   g[G_CY] = -ddy;
+}
+
+// Depth-output terms of a pair under the ray option (where the object-space
+// term decides): z' = z p22 / c with c = p20 dx + p21 dy + p22, so for
+// dz' = dL/dz': dL/dz = dz' p22 / c, dL/dc = -dz' z' / c, and c carries it to
+// p20, p21, p22 and (through dx = px - cx, dy = py - cy) to the center.
+// Replaces the plain-depth term gz = w dD that pair_grads wrote.
+__device__ __forceinline__ void pair_grads_ray_depth(const Pair& e, const float4 qq, float z, float zp, float dzp,
+                                                     float (&g)[16], float& gz) {
+  if (!e.obj) return;
+  const float dc = -dzp * zp * e.rc;
+  gz = dzp * qq.z * e.rc;
+  g[G_P22] += dzp * z * e.rc + dc;
+  g[G_P20] += dc * e.dx;
+  g[G_P21] += dc * e.dy;
+  g[G_CX] -= dc * qq.x;
+  g[G_CY] -= dc * qq.y;
 }
 
 // Dynamic shared memory of the backward kernel (per-pixel arrays indexed by
@@ -661,7 +689,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         const float Tb = tq.x * x;
         const float w = kept ? alpha * Tb : 0.f;
         const float4 col = S.rec.col[j], nrm = S.rec.n[j];
-        const float f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, fmaf(u0.w, col.w,
+        const float4 qj = S.rec.q[j];
+        const float zp = pair_depth(e, col.w, qj.z, P.depth_ray);
+        const float f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, fmaf(u0.w, zp,
                         fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, u1.z * nrm.z))))));
         const float wf = w * f;
         // segmented prefix sum: the sum over entries behind this one
@@ -677,7 +707,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         const float da = Tb * f - (Qb - u1.w) * iom;
         float g[16];
         float gz;
-        pair_grads(e, S.rec.p[j], S.rec.q[j], da, w, u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, P.lp_scale, g, gz);
+        pair_grads(e, S.rec.p[j], qj, da, w, u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, P.lp_scale, g, gz);
+        if (P.depth_ray) pair_grads_ray_depth(e, qj, col.w, zp, w * u0.w, g, gz);
         if (kept) {
           // zero terms (clamped alpha, low-pass pairs) skip their atomic
           float* sg = S.grad + j * SGRAD_STRIDE;

@@ -119,6 +119,7 @@ struct RastParams {
   int32_t tile_w, tile_h;
   int32_t stats;    // keep pair counters
   int32_t fwd_tail; // forward: share the tile's pixels across warps below this many active per warp
+  int32_t depth_ray; // depth output from the ray-splat intersection (SPLAT2D_FLAG_DEPTH_RAY)
 };
 
 // ---------------------------------------------------------------------------

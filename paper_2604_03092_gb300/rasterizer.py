@@ -36,6 +36,7 @@ class RasterConfig:
     stats: bool = True
     fwd_tail: int = 0  # 0: default; 255: forward always shares pixels across warps
     bwd_chunk: int = 64  # 0: same as chunk
+    depth_ray: bool = False  # depth output from the ray-splat intersection (SPLAT2D_FLAG_DEPTH_RAY)
 
     def to_c(self) -> _abi.Config:
         c = _abi.Config()
@@ -44,7 +45,8 @@ class RasterConfig:
         c.lowpass_sigma, c.z_near = self.lowpass_sigma, self.z_near
         for i in range(3):
             c.bg[i] = float(self.bg[i])
-        c.flags = (0 if self.stats else _abi.FLAG_NO_STATS) | ((int(self.fwd_tail) & 0xFF) << 8)
+        c.flags = ((0 if self.stats else _abi.FLAG_NO_STATS) | (_abi.FLAG_DEPTH_RAY if self.depth_ray else 0)
+                   | ((int(self.fwd_tail) & 0xFF) << 8))
         c.bwd_chunk = int(self.bwd_chunk)
         return c
 

@@ -14,7 +14,7 @@ GRAD_REL_L2 = 1e-3     # gradients, relative L2 per parameter group
 def oracle_cfg(cfg: RasterConfig) -> oracle.Config:
     return oracle.Config(alpha_min=cfg.alpha_min, alpha_max=cfg.alpha_max, t_min=cfg.t_min,
                          sigma_lp=cfg.lowpass_sigma, z_near=cfg.z_near, bg=tuple(cfg.bg),
-                         tile_w=cfg.tile_w, tile_h=cfg.tile_h)
+                         tile_w=cfg.tile_w, tile_h=cfg.tile_h, depth_ray=bool(cfg.depth_ray))
 
 
 def to_dev(sc, dev="cuda"):

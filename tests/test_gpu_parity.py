@@ -167,7 +167,7 @@ def test_bin_sort_long_buckets_and_equal_depths(n, tile):
 # forward images
 # --------------------------------------------------------------------------
 
-def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1):
+def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1, extra_flags=0):
     rast, params, im = gpu_forward(sc, cfg)
     ocfg = oracle_cfg(cfg)
     flagged = 0
@@ -177,7 +177,7 @@ def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1):
         p = oracle.preprocess_scene_view(sc, v, ocfg)
         ref = oracle.render(p, mode)
         gpu = view_stack(rast, im, v)
-        ok = (ref.pflags & oracle.PF_FORWARD) == 0
+        ok = (ref.pflags & (oracle.PF_FORWARD | extra_flags)) == 0
         err = np.abs(gpu - ref.out)
         worst = max(worst, float(err[:, ok].max()))
         assert err[:, ok].max() <= FWD_ATOL, (v, np.unravel_index(np.argmax(np.where(ok, err.max(0), 0)), ok.shape),
@@ -192,6 +192,19 @@ def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1):
 def test_forward_random_scene(tile, chunk):
     sc = scenes.random_scene(n=4096, seed=0)
     _check_forward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], chunk=chunk))
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16)])
+def test_forward_ray_depth(tile):
+    # per-pixel ray-splat intersection depth; a tie between the two terms of
+    # the low-pass max flips the depth reading, so such pixels are excluded
+    sc = scenes.random_scene(n=4096, seed=7, scale_range=(0.05, 0.3))
+    _check_forward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], depth_ray=True), extra_flags=oracle.PF_BRANCH)
+
+
+def test_forward_ray_depth_keyframe_views():
+    sc = scenes.keyframe_scene(seed=1001)
+    _check_forward(sc, RasterConfig(depth_ray=True), views=[0, 3], extra_flags=oracle.PF_BRANCH)
 
 
 def test_forward_with_background_and_definition_mode():
@@ -340,6 +353,13 @@ def test_backward_random_scene(seed):
 def test_backward_tile_shapes(tile, chunk, bwd_chunk):
     sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=3, n_views=2)
     _check_backward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], chunk=chunk, bwd_chunk=bwd_chunk))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_backward_ray_depth(seed):
+    sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=20 + seed, n_views=2,
+                             scale_range=(0.03, 0.2))
+    _check_backward(sc, RasterConfig(depth_ray=True, bg=(0.2, 0.1, 0.3)), seed=seed)
 
 
 def test_backward_keyframe_crop():
