@@ -68,6 +68,7 @@ def _load():
         lib.oracle_render_pixels.argtypes = [ctypes.c_int, i64] + [P] * 8 + [i64, P] + [P] * 4
         lib.oracle_render_bwd.argtypes = [ctypes.c_int, i64] + [P] * 9 + [i64, P, P]
         lib.oracle_chain.argtypes = [i64] + [P] * 12
+        lib.oracle_max_error.argtypes = [ctypes.c_int, i64] + [P] * 8 + [P, P]
         lib.oracle_bin_sort.argtypes = [ctypes.c_int] + [P] * 9 + [i64]
         lib.oracle_bin_sort.restype = i64
         _lib = lib
@@ -203,6 +204,19 @@ def render_pixels(prep: Prep, pix: np.ndarray, mode: int = 1):
                              _p(prep.amb), _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), m,
                              _p(pix), _p(out), _p(tf), _p(nb), _p(pf))
     return out, tf, nb, pf
+
+
+def max_error(prep: Prep, err: np.ndarray, mode: int = 1, out: Optional[np.ndarray] = None) -> np.ndarray:
+    """Per surfel, the largest err[y, x] over the pixels that blend it
+    (raised into `out` if given, else into zeros)."""
+    lib = _load()
+    W, H = int(prep.cam[0]), int(prep.cam[1])
+    err = _c(np.broadcast_to(err, (H, W)), np.float64)
+    n = prep.rec.shape[0]
+    out = np.zeros(n) if out is None else out
+    lib.oracle_max_error(mode, n, _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb), _p(prep.zbits),
+                         _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(err), _p(out))
+    return out
 
 
 @dataclass

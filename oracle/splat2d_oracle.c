@@ -605,6 +605,42 @@ int oracle_render_pixels(int mode, int64_t n, const double* rec, const int32_t* 
 }
 
 /*
+ * Error attribution for pruning (Sec. 4.3, "Map Fusion": primitives that
+ * contribute to pixels with high RGB or depth error are removed).  Reading:
+ * a surfel contributes to a pixel when the pixel blends it (alpha >=
+ * alpha_min, before the pixel's stop); for each surfel, max_err[s] is raised
+ * to the largest err[p] over the pixels p it contributes to.  err is a
+ * caller-given per-pixel error [H][W] (>= 0).  Pixels are walked one by one.
+ */
+int oracle_max_error(int mode, int64_t n, const double* rec, const int32_t* status, const int32_t* pixrect,
+                     const int32_t* amb, const uint32_t* zbits, const uint32_t* sflags, const double* camv,
+                     const double* cfgv, const double* err, double* max_err) {
+  cam_t cam;
+  cfg_t cfg;
+  load_cam(camv, &cam);
+  load_cfg(cfgv, &cfg);
+  view_t V;
+  build_view(&V, mode, n, rec, status, pixrect, amb, zbits, sflags, &cam, &cfg);
+  int64_t cap = 4096;
+  blend_t* list = (blend_t*)malloc(sizeof(blend_t) * cap);
+  for (int iy = 0; iy < cam.H; iy++)
+    for (int ix = 0; ix < cam.W; ix++) {
+      int64_t nb = walk_pixel(&V, &cfg, ix, iy, NULL, NULL, NULL, NULL, list, cap);
+      if (nb > cap) {
+        cap = nb;
+        list = (blend_t*)realloc(list, sizeof(blend_t) * cap);
+        nb = walk_pixel(&V, &cfg, ix, iy, NULL, NULL, NULL, NULL, list, cap);
+      }
+      double e = err[(int64_t)iy * cam.W + ix];
+      for (int64_t k = 0; k < nb; k++)
+        if (e > max_err[list[k].s]) max_err[list[k].s] = e;
+    }
+  free(list);
+  free_view(&V);
+  return 0;
+}
+
+/*
  * Reverse pass of one view.  Upstream gradients g8 are [8][H][W] (same
  * channel order as the outputs).  Record gradients (dL/d of the 19 record
  * fields) are accumulated into grec[n*20]; the chain rule to the surfel

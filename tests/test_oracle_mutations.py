@@ -34,6 +34,8 @@ MUTATIONS = [
      "dM[i * 3 + j] += gr[R_DET] * g.A[i * 3 + j];"),
     ("ray depth where the low-pass term decides", "e->zray = cfg->depth_ray && e->obj && e->c != 0;",
      "e->zray = cfg->depth_ray && e->c != 0;"),
+    ("error attribution summed", "if (e > max_err[list[k].s]) max_err[list[k].s] = e;",
+     "max_err[list[k].s] += e;"),
 ]
 
 

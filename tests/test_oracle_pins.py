@@ -417,6 +417,53 @@ def test_bin_sort_is_a_stable_sort_of_the_rect_instances():
 
 
 # --------------------------------------------------------------------------
+# error attribution for pruning (Sec. 4.3, Map Fusion)
+# --------------------------------------------------------------------------
+
+def test_max_error_single_surfel_is_max_over_its_footprint():
+    """One surfel: the pixels that blend it are exactly those where the
+    image's alpha is nonzero, so its attributed error is the maximum of the
+    error map there."""
+    rng = np.random.default_rng(5)
+    view = _view(W=30, H=22, f=28.0)
+    cfg = oracle.Config()
+    im, p = _render([0.02, 0.01, 2.0], [0.15, 0.09], rng.normal(size=4), 0.8, [0.3, 0.6, 0.9], view, cfg)
+    err = rng.uniform(0, 1, (view.height, view.width))
+    got = oracle.max_error(p, err)
+    cov = im.alpha > 0
+    assert cov.sum() > 10
+    assert got[0] == err[cov].max()
+    assert oracle.max_error(p, np.where(cov, 0.0, err))[0] == 0.0
+
+
+def test_max_error_respects_occlusion_stop():
+    """Two surfels on the optical axis, the nearer one in front; with
+    t_min = 0.2 a pixel stops before the back surfel wherever the front one
+    has taken T to 1 - a1 and (1 - a1)(1 - a2) < 0.2 (composited here from
+    each surfel's own alpha map), so the back surfel is charged only the
+    error of pixels where it is actually blended."""
+    view = _view(W=24, H=24, f=30.0)
+    cfg = oracle.Config(t_min=0.2, sigma_lp=0.0)
+    q = [1.0, 0.0, 0.0, 0.0]
+    front = ([0.0, 0.0, 2.0], [0.12, 0.12], q, 0.7)
+    back = ([0.0, 0.0, 3.0], [0.25, 0.25], q, 0.7)
+    a = [_render(m, s_, q_, o, [1, 1, 1], view, oracle.Config(t_min=1e-4, sigma_lp=0.0))[0].alpha
+         for m, s_, q_, o in (front, back)]
+    blend_f = (a[0] > 0) & ((1 - a[0]) >= cfg.t_min)
+    t_after = np.where(blend_f, 1 - a[0], 1.0)
+    blend_b = (a[1] > 0) & (t_after * (1 - a[1]) >= cfg.t_min)
+    assert (a[1] > 0).sum() > blend_b.sum() > 0  # the stop hides part of the back surfel
+    err = np.random.default_rng(6).uniform(0, 1, (24, 24))
+    err[12, 12] = 5.0  # under both surfels, where the back one is never blended
+    assert not blend_b[12, 12] and blend_f[12, 12]
+    _, p = _render(np.array([front[0], back[0]]), np.array([front[1], back[1]]), np.array([q, q]),
+                   [0.7, 0.7], np.ones((2, 3)), view, cfg)
+    got = oracle.max_error(p, err)
+    assert got[0] == err[blend_f].max() == 5.0
+    assert got[1] == err[blend_b].max() < 5.0
+
+
+# --------------------------------------------------------------------------
 # gradients: FP64 central differences and rigid-motion identities
 # --------------------------------------------------------------------------
 
