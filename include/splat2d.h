@@ -204,10 +204,10 @@ int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, v
 /*
  * Reverse pass: walks each pixel back to front from its last blended surfel,
  * recovering the transmittance by division instead of storing per-pixel
- * lists; per-surfel gradients are summed across each warp with shuffles and
- * across the tile in shared memory before one vector atomic per (tile,
- * surfel); then a per-surfel pass chains them to the parameters and reduces
- * the per-view pose tangent.  d_* are upstream gradients laid out like the
+ * lists (32 (pixel, surfel) pairs per warp step, with segmented warp scans);
+ * per-surfel gradients are summed across the tile in shared memory before
+ * one vector atomic per (tile, surfel); then a per-surfel pass chains them to
+ * the parameters and reduces the per-view pose tangent.  d_* are upstream gradients laid out like the
  * forward outputs (NULL = zero).  Must follow splat2d_render_fwd on the same
  * workspace with unchanged surfels.
  */
@@ -228,6 +228,41 @@ int splat2d_render_bwd_tiles(const splat2d_config* cfg, const splat2d_problem* p
                              splat2d_stream stream);
 int splat2d_preprocess_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
                            void* ws, size_t ws_bytes, const splat2d_grads* grads, splat2d_stream stream);
+
+/*
+ * Map fusion, pruning input (Sec. 4.3, "Map Fusion": the global map is
+ * rendered at the new keyframe's pose and primitives that contribute to
+ * pixels with high RGB or depth error are removed).  For every (pixel,
+ * surfel) pair the forward blended -- an entry of the pixel's tile list
+ * before its last blended entry whose alpha there is at least alpha_min --
+ * max_err[surfel] = max(max_err[surfel], err[pixel]).
+ *   err      device, one float per packed pixel (laid out like the alpha
+ *            output); values <= 0 and NaN count as zero.
+ *   max_err  device, [n_surfels] floats, initialised by the caller (zeros,
+ *            or the result of earlier calls) to values >= 0; only raised.
+ * Must follow splat2d_render_fwd on the same workspace.  The caller prunes
+ * the surfels whose max_err exceeds its threshold.  NULL pointers give
+ * SPLAT2D_ERR_INVALID_ARG; after an instance-capacity overflow (device
+ * status) the call does nothing.
+ */
+int splat2d_max_error(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                      const float* err, float* max_err, splat2d_stream stream);
+
+/*
+ * Map fusion, insertion gate (Sec. 4.3, "Map Fusion": new primitives are
+ * added only where the accumulation map rendered from the global map is
+ * below a threshold tau_accum).
+ *   alpha     device, n floats: the forward's alpha output at the new
+ *             keyframe's pose, one per pixel (= per new per-pixel primitive).
+ *   keep_idx  device, capacity n: receives the ascending indices i with
+ *             alpha[i] < tau (NaN is never kept).
+ *   n_keep    device int64: receives their number.
+ *   tmp       device scratch of splat2d_accum_gate_tmp_size(n) bytes.
+ * 0 <= n < 2^32.  Asynchronous on `stream`; no allocation.
+ */
+size_t splat2d_accum_gate_tmp_size(int64_t n);
+int splat2d_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_idx, int64_t* n_keep, void* tmp,
+                       size_t tmp_bytes, splat2d_stream stream);
 
 /* Number of kernels this library has enqueued since it was loaded (host-side
  * count, including launches recorded into a CUDA graph). */

@@ -219,6 +219,14 @@ def max_error(prep: Prep, err: np.ndarray, mode: int = 1, out: Optional[np.ndarr
     return out
 
 
+def accum_gate(alpha: np.ndarray, tau: float) -> np.ndarray:
+    """Insertion gate of map fusion (Sec. 4.3, "Map Fusion"): new per-pixel
+    primitives go only where the accumulated alpha rendered from the global
+    map is below tau.  Ascending indices i with alpha[i] < tau (NaN never)."""
+    a = np.asarray(alpha).reshape(-1)
+    return np.nonzero(a < tau)[0]
+
+
 @dataclass
 class Grads:
     means: np.ndarray

@@ -80,6 +80,11 @@ SIGNATURES = {
     "splat2d_preprocess_bwd": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem),
                                               ctypes.POINTER(Surfels), c_void_p, c_size_t, ctypes.POINTER(Grads),
                                               c_void_p]),
+    "splat2d_max_error": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem), c_void_p, c_size_t,
+                                         c_void_p, c_void_p, c_void_p]),
+    "splat2d_accum_gate_tmp_size": (c_size_t, [c_int64]),
+    "splat2d_accum_gate": (ctypes.c_int, [c_void_p, c_int64, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_size_t,
+                                          c_void_p]),
     "splat2d_launch_count": (ctypes.c_uint64, []),
     "splat2d_stats": (ctypes.c_int, [c_void_p, ctypes.POINTER(Stats), c_void_p]),
     "splat2d_status": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64), c_void_p]),

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsplat2d.so")
-SOURCES = ["preprocess.cu", "binsort.cu", "render.cu", "api.cu", "sort_static.cu"]
+SOURCES = ["preprocess.cu", "binsort.cu", "render.cu", "fusion.cu", "api.cu", "sort_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

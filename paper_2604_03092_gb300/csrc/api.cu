@@ -331,6 +331,32 @@ int splat2d_preprocess_bwd(const splat2d_config* cfg, const splat2d_problem* pro
   return SPLAT2D_OK;
 }
 
+int splat2d_max_error(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                      const float* err, float* max_err, splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  if (!err || !max_err) return SPLAT2D_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
+  if (launch_max_error(L, make_params(cfg), cfg->chunk, w, vals, err, max_err, st) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+size_t splat2d_accum_gate_tmp_size(int64_t n) { return n < 0 ? 0 : accum_gate_tmp_size(n); }
+
+int splat2d_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_idx, int64_t* n_keep, void* tmp,
+                       size_t tmp_bytes, splat2d_stream stream) {
+  if (n < 0 || n > (int64_t)0xFFFFFFFFll || !n_keep) return SPLAT2D_ERR_INVALID_ARG;
+  if (n > 0 && (!alpha || !keep_idx || !tmp)) return SPLAT2D_ERR_INVALID_ARG;
+  if (n > 0 && tmp_bytes < accum_gate_tmp_size(n)) return SPLAT2D_ERR_WORKSPACE_TOO_SMALL;
+  if (launch_accum_gate(alpha, n, tau, keep_idx, n_keep, tmp, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
 int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
                        void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
                        const float* d_alpha, const splat2d_grads* grads, splat2d_stream stream) {

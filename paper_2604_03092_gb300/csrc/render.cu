@@ -761,6 +761,90 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
 }
 
 // ---------------------------------------------------------------------------
+// Error attribution for pruning (Sec. 4.3, "Map Fusion": primitives that
+// contribute to pixels with high RGB or depth error are removed).  A surfel
+// contributes to a pixel when the pixel blends it: an entry of the pixel's
+// tile list before the pixel's `last` (left by the forward) whose alpha there
+// is at least alpha_min.  For every such pair the surfel's attributed error
+// is raised to the pixel's error.  Errors are compared as the bit patterns of
+// non-negative floats (ordered like the values), first per tile in shared
+// memory, then once per (tile, surfel) with a global atomicMax.
+// ---------------------------------------------------------------------------
+template <int CHUNK>
+struct ErrSmem {
+  SRecs<CHUNK> rec;
+  uint32_t emax[CHUNK];  // per entry of the chunk: largest error bits of a pixel that blends it
+  int item;
+  uint32_t top;
+};
+
+template <int TW, int TH, int CHUNK>
+__global__ void __launch_bounds__(TW* TH) k_max_error(const RenderArgs A, const float* __restrict__ err,
+                                                      uint32_t* __restrict__ max_err) {
+  constexpr int NT = TW * TH, WX = TW / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ErrSmem<CHUNK>& S = *reinterpret_cast<ErrSmem<CHUNK>*>(smem_raw);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const RastParams& P = A.P;
+  if (A.hdr->status != 0) return;
+  for (;;) {
+    if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_aux, 1u);
+    __syncthreads();
+    const int item = S.item;
+    if (item >= A.T) break;
+    const int t = (int)__ldg(A.order + item);
+    const int v = find_view_by_tile(A.views, A.V, t);
+    const DView& vw = A.views[v];
+    const int lt = t - vw.tile_base;
+    const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
+    const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
+    const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
+    const bool inside = ipx < vw.W && ipy < vw.H;
+    const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
+    const uint2 range = __ldg(A.ranges + t);
+    uint32_t my_last = range.x, ebits = 0u;
+    if (inside) {
+      const int64_t pix = vw.poff + (int64_t)ipy * vw.W + ipx;
+      const float e = err[pix];
+      ebits = e > 0.f ? __float_as_uint(e) : 0u;  // negative and NaN errors count as zero
+      if (ebits) my_last = A.last[pix];
+    }
+    if (threadIdx.x == 0) S.top = range.x;
+    __syncthreads();
+    if (my_last > range.x) atomicMax(&S.top, my_last);
+    __syncthreads();
+    const uint32_t top = S.top;
+    __syncthreads();
+    for (int64_t lo = range.x; lo < (int64_t)top; lo += CHUNK) {
+      const int count = (int)min64(CHUNK, (int64_t)top - lo);
+      const int nwd = (count + 31) >> 5;
+      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, nullptr);
+      for (int j = threadIdx.x; j < count; j += NT) S.emax[j] = 0u;
+      __syncthreads();
+      const int lim = (int)min64(max64((int64_t)my_last - lo, 0), count);
+      for (int wd = 0; wd < nwd; wd++) {
+        uint32_t b = lane_word(S.rec, wd, count, bx, by, lane);
+        const int keep = lim - wd * 32;
+        b = keep >= 32 ? b : (keep <= 0 ? 0u : (b & ((1u << keep) - 1u)));
+        while (b) {
+          const int j = wd * 32 + __ffs(b) - 1;
+          b &= b - 1;
+          Pair e;
+          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], px, py, P.lp_scale, P.alpha_max, e);
+          if (e.alpha >= P.alpha_min) atomicMax(&S.emax[j], ebits);
+        }
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < count; j += NT) {
+        const uint32_t m = S.emax[j];
+        if (m) atomicMax(max_err + __ldg(A.vals + lo + j), m);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launch
 // ---------------------------------------------------------------------------
 static RenderArgs make_args(const Layout& L, const RastParams& P, char* ws, const uint32_t* vals) {
@@ -823,6 +907,22 @@ static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int TW, int TH, int CHUNK>
+static cudaError_t run_max_error(const RenderArgs& A, const float* err, uint32_t* max_err, cudaStream_t st) {
+  auto k = k_max_error<TW, TH, CHUNK>;
+  constexpr size_t smem = sizeof(ErrSmem<CHUNK>);
+  static int grid = -1;
+  static int64_t grid_T = -1;
+  if (grid < 0) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (grid < 0 || grid_T != A.T) {
+    grid = persistent_grid(k, TW * TH, smem, A.T);
+    grid_T = A.T;
+  }
+  k<<<grid, TW * TH, smem, st>>>(A, err, max_err);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 #define S2D_DISPATCH(FN, TWv, THv, CH, ...)                                   \
   do {                                                                        \
     if (TWv == 16 && THv == 16) {                                             \
@@ -870,6 +970,17 @@ cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, c
   cudaError_t e = cudaMemsetAsync(&hdr->queue_bwd, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   S2D_DISPATCH(run_bwd, P.tile_w, P.tile_h, chunk, A, st);
+}
+
+cudaError_t launch_max_error(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
+                             const float* err, float* max_err, cudaStream_t st) {
+  if (L.T <= 0) return cudaSuccess;
+  RenderArgs A = make_args(L, P, ws, vals);
+  Header* hdr = reinterpret_cast<Header*>(ws + L.header);
+  cudaError_t e = cudaMemsetAsync(&hdr->queue_aux, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  uint32_t* m = reinterpret_cast<uint32_t*>(max_err);
+  S2D_DISPATCH(run_max_error, P.tile_w, P.tile_h, chunk, A, err, m, st);
 }
 
 }  // namespace s2d

@@ -52,7 +52,8 @@ struct Header {
   unsigned long long n_visible;  // visible (view, surfel) pairs
   uint32_t queue_fwd, queue_bwd; // persistent work queues
   unsigned long long stat[8];    // pair counters, see STAT_*
-  uint32_t pad[32];
+  uint32_t queue_aux;            // work queue of the error-attribution pass
+  uint32_t pad[31];
 };
 static_assert(sizeof(Header) <= 256, "Header layout");
 enum { STAT_FWD_EVAL = 0, STAT_FWD_BLEND = 1, STAT_BWD_EVAL = 2, STAT_BWD_BLEND = 3 };
@@ -138,6 +139,11 @@ cudaError_t launch_render_fwd(const Layout& L, const RastParams& P, int chunk, c
 cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
                               const float* d_rgb, const float* d_depth, const float* d_normal,
                               const float* d_alpha, cudaStream_t st);
+cudaError_t launch_max_error(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
+                             const float* err, float* max_err, cudaStream_t st);
+cudaError_t launch_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_idx, int64_t* n_keep,
+                              void* tmp, cudaStream_t st);
+size_t accum_gate_tmp_size(int64_t n);
 cudaError_t launch_preprocess_bwd(const splat2d_surfels* S, const Layout& L, const RastParams& P, char* ws,
                                   const splat2d_grads* G, bool atomic_params, cudaStream_t st);
 int sm_count();

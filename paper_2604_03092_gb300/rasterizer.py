@@ -17,7 +17,7 @@ import torch
 
 from . import _abi
 
-__all__ = ["RasterConfig", "Rasterizer", "Images", "SurfelGrads", "Splat2DRender", "render"]
+__all__ = ["RasterConfig", "Rasterizer", "Images", "SurfelGrads", "Splat2DRender", "render", "accum_gate"]
 
 
 @dataclasses.dataclass
@@ -237,6 +237,20 @@ class Rasterizer:
                                                      self.ws_bytes, d[0], d[1], d[2], d[3], _stream()),
                    "splat2d_render_bwd_tiles")
 
+    def max_error(self, err: torch.Tensor, max_err: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Map-fusion pruning input: per surfel, the largest err over the
+        pixels that blended it in the last forward (err packed like the
+        alpha output).  Raised into `max_err` (zeros if not given)."""
+        err = err.contiguous().view(-1)
+        if err.numel() != self.n_pixels or err.dtype != torch.float32:
+            raise ValueError("err: one float32 per packed pixel")
+        if max_err is None:
+            max_err = torch.zeros(self.n_surfels, device=self.device)
+        _abi.check(self.lib.splat2d_max_error(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
+                                              self.ws_bytes, _ptr(err), _ptr(max_err), _stream()),
+                   "splat2d_max_error")
+        return max_err
+
     def preprocess_bwd(self, means, scales, quats, opacity, rgb, grads: SurfelGrads):
         """Chain rule from the workspace's record gradients to `grads`."""
         sf = self._surfels(means, scales, quats, opacity, rgb)
@@ -296,6 +310,23 @@ class Rasterizer:
         flat = [None if t is None else t.contiguous().view(-1) for t in d_out]
         self.render_bwd(means, scales, quats, opacity, rgb, flat, grads)
         return grads
+
+
+def accum_gate(alpha: torch.Tensor, tau: float):
+    """Map-fusion insertion gate: (keep_idx, n_keep) with keep_idx[:n_keep]
+    the ascending indices of the pixels whose accumulated alpha is below
+    tau; n_keep is a device tensor (read it to slice; no sync here)."""
+    lib = _abi.load()
+    alpha = alpha.contiguous().view(-1)
+    if alpha.dtype != torch.float32 or not alpha.is_cuda:
+        raise ValueError("alpha: float32 CUDA tensor")
+    n = alpha.numel()
+    keep = torch.empty(max(n, 1), dtype=torch.int32, device=alpha.device)
+    n_keep = torch.zeros(1, dtype=torch.int64, device=alpha.device)
+    tmp = torch.empty(max(int(lib.splat2d_accum_gate_tmp_size(n)), 4), dtype=torch.uint8, device=alpha.device)
+    _abi.check(lib.splat2d_accum_gate(_ptr(alpha), n, float(tau), keep.data_ptr(), n_keep.data_ptr(),
+                                      tmp.data_ptr(), tmp.numel(), _stream()), "splat2d_accum_gate")
+    return keep, n_keep
 
 
 class Splat2DRender(torch.autograd.Function):

@@ -463,6 +463,18 @@ def test_max_error_respects_occlusion_stop():
     assert got[1] == err[blend_b].max() < 5.0
 
 
+def test_accum_gate_brute_force():
+    """The insertion gate keeps exactly the pixels below the threshold, in
+    order (a pixel-by-pixel loop)."""
+    rng = np.random.default_rng(8)
+    a = rng.uniform(0, 1, 200)
+    a[::9] = 0.3
+    a[5::13] = np.nan
+    expect = [i for i in range(a.size) if a[i] == a[i] and a[i] < 0.3]
+    assert list(oracle.accum_gate(a, 0.3)) == expect
+    assert oracle.accum_gate(np.zeros(0), 0.5).size == 0
+
+
 # --------------------------------------------------------------------------
 # gradients: FP64 central differences and rigid-motion identities
 # --------------------------------------------------------------------------
