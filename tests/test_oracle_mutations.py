@@ -51,3 +51,28 @@ def test_pins_catch_planted_mistake(tmp_path, name, orig, bad):
     r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
                         "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
+
+
+# planted mistakes in the map-maintenance statements (oracle/fusion.py)
+FUSION_MUTATIONS = [
+    ("quaternion alignment dropped", "acc += q if np.dot(q, q1) >= 0 else -q", "acc += q"),
+    ("scales left unscaled", "s2[i] = s * np.asarray(scales[i], np.float64)", "s2[i] = np.asarray(scales[i], np.float64)"),
+    ("rotation product order", "q2[i] = quat_mul(q / np.linalg.norm(q), np.asarray(quats[i], np.float64))",
+     "q2[i] = quat_mul(np.asarray(quats[i], np.float64), q / np.linalg.norm(q))"),
+    ("depth gate inverted", "if max(z) - min(z) > tau_d:", "if max(z) - min(z) < tau_d:"),
+    ("edge block size", "n = len(idx)", "n = 4"),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,orig,bad", FUSION_MUTATIONS, ids=[m[0] for m in FUSION_MUTATIONS])
+def test_fusion_pins_catch_planted_mistake(tmp_path, name, orig, bad):
+    src = open(os.path.join(ROOT, "oracle", "fusion.py")).read()
+    assert orig in src, f"mutation anchor for {name!r} no longer in the oracle"
+    for d in ("oracle", "tests", "paper_2604_03092_gb300"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d,
+                        ignore=shutil.ignore_patterns("_lib", "__pycache__", "golden"))
+    (tmp_path / "oracle" / "fusion.py").write_text(src.replace(orig, bad))
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_fusion.py", "-q", "-x",
+                        "-p", "no:cacheprovider"], cwd=tmp_path, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
