@@ -91,6 +91,16 @@ typedef struct {
   int64_t n;
 } splat2d_surfels;
 
+/* Writable surfel arrays (device, FP32, row-major), for the map-maintenance
+ * calls that produce or update surfels in place. */
+typedef struct {
+  float* means;    /* [N, 3] */
+  float* scales;   /* [N, 2] */
+  float* quats;    /* [N, 4] (w, x, y, z) */
+  float* opacity;  /* [N] */
+  float* rgb;      /* [N, 3] */
+} splat2d_surfel_buffers;
+
 /* Gradient outputs (device arrays).  Accumulated into (+=): zero them first.
  * Any pointer may be NULL to skip that output. */
 typedef struct {
@@ -263,6 +273,42 @@ int splat2d_max_error(const splat2d_config* cfg, const splat2d_problem* prob, vo
 size_t splat2d_accum_gate_tmp_size(int64_t n);
 int splat2d_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_idx, int64_t* n_keep, void* tmp,
                        size_t tmp_bytes, splat2d_stream stream);
+
+/*
+ * Adaptive voxelization of a keyframe's per-pixel map (Sec. 4.3, "Adaptive
+ * Voxelization").  in: the keyframe's primitives, one per pixel, index
+ * y * width + x (in->n must equal width * height), centers in the
+ * keyframe's camera frame.  The map is cut into 2x2 blocks of primitives
+ * (ragged blocks at odd edges); a block becomes one primitive with the mean
+ * center, opacity, colour and tangent scales of its primitives and the
+ * normalised sum of their quaternions, each first negated if its dot
+ * product with the block's first quaternion is negative; a block whose
+ * camera-frame depth range (max - min of mu.z) exceeds tau_d keeps its
+ * primitives unchanged.  Writes, in order (blocks row-major; a kept block's
+ * primitives row-major), the primitives to out (device arrays with capacity
+ * width * height), their block index to out_block (device int32, may be
+ * NULL), and their number to *n_out (device int64).  tmp: device scratch of
+ * splat2d_voxelize_tmp_size(width, height) bytes.  No allocation, async.
+ */
+size_t splat2d_voxelize_tmp_size(int32_t width, int32_t height);
+int splat2d_voxelize(const splat2d_surfels* in, int32_t width, int32_t height, float tau_d,
+                     const splat2d_surfel_buffers* out, int32_t* out_block, int64_t* n_out, void* tmp,
+                     size_t tmp_bytes, splat2d_stream stream);
+
+/*
+ * Sim(3) transform of primitives, in place (Sec. 4.3: "Map Fusion" moves a
+ * keyframe's primitives from its camera frame to the world with the
+ * keyframe's Sim(3) pose, mu' = s R mu + t and r' = q r; "Loop Correction of
+ * Gaussian Map" applies to each keyframe's primitives the change of its
+ * pose, Delta T = T_new T_old^-1).  sim3: device, [K, 8] rows (qw, qx, qy,
+ * qz, tx, ty, tz, s), q any nonzero norm (normalised inside).  index:
+ * device int32 [n] choosing each primitive's row (the keyframe it is bound
+ * to), or NULL for row 0.  means, quats, scales: device arrays of n
+ * primitives, updated in place (any may be NULL to leave it); quats become
+ * q r (Hamilton product, not renormalised); scales are multiplied by s.
+ */
+int splat2d_sim3_apply(int64_t n, float* means, float* quats, float* scales, const float* sim3,
+                       const int32_t* index, splat2d_stream stream);
 
 /* Number of kernels this library has enqueued since it was loaded (host-side
  * count, including launches recorded into a CUDA graph). */

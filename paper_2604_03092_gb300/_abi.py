@@ -44,6 +44,11 @@ class Config(ctypes.Structure):
                 ("bg", c_float * 3), ("flags", c_uint32), ("bwd_chunk", c_int32)]
 
 
+class SurfelBuffers(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p), ("opacity", c_void_p),
+                ("rgb", c_void_p)]
+
+
 class Problem(ctypes.Structure):
     _fields_ = [("views", ctypes.POINTER(View)), ("n_views", c_int32), ("n_surfels", c_int64),
                 ("instance_capacity", c_int64)]
@@ -85,6 +90,11 @@ SIGNATURES = {
     "splat2d_accum_gate_tmp_size": (c_size_t, [c_int64]),
     "splat2d_accum_gate": (ctypes.c_int, [c_void_p, c_int64, ctypes.c_float, c_void_p, c_void_p, c_void_p, c_size_t,
                                           c_void_p]),
+    "splat2d_voxelize_tmp_size": (c_size_t, [ctypes.c_int32, ctypes.c_int32]),
+    "splat2d_voxelize": (ctypes.c_int, [ctypes.POINTER(Surfels), ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                                        ctypes.POINTER(SurfelBuffers), c_void_p, c_void_p, c_void_p, c_size_t,
+                                        c_void_p]),
+    "splat2d_sim3_apply": (ctypes.c_int, [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "splat2d_launch_count": (ctypes.c_uint64, []),
     "splat2d_stats": (ctypes.c_int, [c_void_p, ctypes.POINTER(Stats), c_void_p]),
     "splat2d_status": (ctypes.c_int, [c_void_p, ctypes.POINTER(c_int64), c_void_p]),

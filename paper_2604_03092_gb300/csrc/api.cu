@@ -357,6 +357,35 @@ int splat2d_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_
   return SPLAT2D_OK;
 }
 
+size_t splat2d_voxelize_tmp_size(int32_t width, int32_t height) {
+  return (width < 0 || height < 0) ? 0 : voxelize_tmp_size(width, height);
+}
+
+int splat2d_voxelize(const splat2d_surfels* in, int32_t width, int32_t height, float tau_d,
+                     const splat2d_surfel_buffers* out, int32_t* out_block, int64_t* n_out, void* tmp,
+                     size_t tmp_bytes, splat2d_stream stream) {
+  if (!in || !out || !n_out || width < 0 || height < 0) return SPLAT2D_ERR_INVALID_ARG;
+  if (in->n != (int64_t)width * height || (int64_t)width * height > (int64_t)0x7FFFFFFF) return SPLAT2D_ERR_INVALID_ARG;
+  if (in->n > 0) {
+    if (!in->means || !in->scales || !in->quats || !in->opacity || !in->rgb) return SPLAT2D_ERR_INVALID_ARG;
+    if (!out->means || !out->scales || !out->quats || !out->opacity || !out->rgb || !tmp)
+      return SPLAT2D_ERR_INVALID_ARG;
+    if (tmp_bytes < voxelize_tmp_size(width, height)) return SPLAT2D_ERR_WORKSPACE_TOO_SMALL;
+  }
+  if (launch_voxelize(*in, width, height, tau_d, *out, out_block, n_out, tmp, reinterpret_cast<cudaStream_t>(stream)) !=
+      cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_sim3_apply(int64_t n, float* means, float* quats, float* scales, const float* sim3,
+                       const int32_t* index, splat2d_stream stream) {
+  if (n < 0 || (n > 0 && !sim3)) return SPLAT2D_ERR_INVALID_ARG;
+  if (launch_sim3(n, means, quats, scales, sim3, index, reinterpret_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
 int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
                        void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
                        const float* d_alpha, const splat2d_grads* grads, splat2d_stream stream) {

@@ -144,6 +144,12 @@ cudaError_t launch_max_error(const Layout& L, const RastParams& P, int chunk, ch
 cudaError_t launch_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_idx, int64_t* n_keep,
                               void* tmp, cudaStream_t st);
 size_t accum_gate_tmp_size(int64_t n);
+size_t voxelize_tmp_size(int32_t W, int32_t H);
+cudaError_t launch_voxelize(const splat2d_surfels& in, int32_t W, int32_t H, float tau_d,
+                            const splat2d_surfel_buffers& out, int32_t* out_block, int64_t* n_out, void* tmp,
+                            cudaStream_t st);
+cudaError_t launch_sim3(int64_t n, float* means, float* quats, float* scales, const float* sim3, const int32_t* index,
+                        cudaStream_t st);
 cudaError_t launch_preprocess_bwd(const splat2d_surfels* S, const Layout& L, const RastParams& P, char* ws,
                                   const splat2d_grads* G, bool atomic_params, cudaStream_t st);
 int sm_count();
