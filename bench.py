@@ -201,6 +201,61 @@ def run_reference(args, wl_desc, make):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
+def _time_maintenance(rast, params, sc, out, dev, hbm_gbs, reps: int = 5):
+    """CUDA-event times of the map-maintenance kernels on this workload:
+    error attribution over all views (after a forward), the accumulation
+    gate on one view's alpha, 2x2 voxelization of one keyframe-sized
+    per-pixel map, and a per-keyframe Sim(3) correction of every surfel."""
+    import torch
+
+    from paper_2604_03092_gb300 import mapping
+    from paper_2604_03092_gb300.rasterizer import accum_gate
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    res = {}
+    rast.forward(*params, out=out, check=False)
+    err = torch.rand(rast.n_pixels, device=dev)
+    max_err = torch.zeros(rast.n_surfels, device=dev)
+    res["max_error_ms"] = timed(lambda: rast.max_error(err, max_err))
+    H, W = rast.sizes[0]
+    alpha0 = out.alpha[:H * W]
+    res["accum_gate_ms"] = timed(lambda: accum_gate(alpha0, 0.5))
+    n = H * W
+    g = torch.Generator(device=dev).manual_seed(0)
+    m = torch.rand(n, 3, device=dev, generator=g) + torch.tensor([0.0, 0.0, 1.0], device=dev)
+    q = torch.randn(n, 4, device=dev, generator=g)
+    s_ = torch.rand(n, 2, device=dev, generator=g) * 0.01
+    o = torch.rand(n, device=dev, generator=g)
+    c = torch.rand(n, 3, device=dev, generator=g)
+    vox_ms = timed(lambda: mapping.voxelize(m, q, s_, o, c, W, H, 0.05))
+    res["voxelize_ms"] = vox_ms
+    (_, _, _, _, _), _, n_out = mapping.voxelize(m, q, s_, o, c, W, H, 0.05)
+    vox_bytes = 56 * n + 52 * int(n_out.item())  # attributes read (depths twice) + merged map written
+    res["voxelize_hbm_frac"] = vox_bytes / (vox_ms / 1e3) / 1e9 / hbm_gbs
+    N = rast.n_surfels
+    mm, qq, ss = params[0].clone(), params[2].clone(), params[1].clone()
+    kf = len(sc.views)
+    sim3 = torch.cat([torch.randn(kf, 4, device=dev, generator=g), torch.randn(kf, 3, device=dev, generator=g) * 0.01,
+                      torch.ones(kf, 1, device=dev)], 1).contiguous()
+    index = (torch.arange(N, device=dev) * kf // N).to(torch.int32)
+    sim_ms = timed(lambda: mapping.sim3_apply(mm, qq, ss, sim3, index))
+    res["sim3_ms"] = sim_ms
+    res["sim3_hbm_frac"] = (2 * 36 + 4) * N / (sim_ms / 1e3) / 1e9 / hbm_gbs
+    res["note"] = (f"error attribution over {kf} views x {H}x{W}; gate on one {H}x{W} alpha map; voxelization of one "
+                   f"{W}x{H} per-pixel map; Sim(3) of {N} surfels bound to {kf} keyframes")
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,6 +273,7 @@ def main():
     ap.add_argument("--ref-pixels", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-json", default=None, help="ncu DRAM-byte summary for the roofline kernel")
+    ap.add_argument("--no-maintenance", action="store_true", help="skip timing the map-maintenance kernels")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -425,6 +481,11 @@ def main():
     e2e_vps = multirank.whole_job_rate(multirank.sum_over_ranks(V * args.e2e_steps, dev),
                                        multirank.max_over_ranks(e2e_ms, dev))
 
+    # ---- map maintenance around the refinement (Sec. 4.3), on this workload ---
+    maint = None
+    if not args.no_maintenance and rank == 0:
+        maint = _time_maintenance(rast, params, sc, out, dev, _peaks()["hbm_gbs"])
+
     # ---- roofline of the dominant stage ------------------------------------------
     peaks = _peaks()
     clocks = clk.summary()
@@ -498,6 +559,7 @@ def main():
             "pairs": {k: st[k] for k in ("fwd_pairs_evaluated", "fwd_pairs_blended", "bwd_pairs_evaluated",
                                          "bwd_pairs_blended")},
             "cpu_baseline": cpu,
+            "map_maintenance": maint,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
