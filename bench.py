@@ -139,33 +139,26 @@ def _peaks() -> dict:
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
-def oracle_sample(sc, n_pix: int, seed: int = 0):
-    """Time the FP64 oracle on one view of the workload: full preprocess of the
-    view's surfel range, forward at n_pix sampled pixels, reverse pass at the
-    same pixels, chain rule; returns (seconds per view extrapolated to every
-    pixel, description)."""
+def oracle_views(sc, views, seed: int = 0):
+    """Time the FP64 oracle, as it stands, on whole views of the workload:
+    per view the preprocess of its surfel range, the forward at every pixel
+    and the reverse pass at every pixel (seeded upstream gradient) with the
+    chain rule.  Returns (seconds per view, description, wall seconds)."""
     import oracle
-    v = 0
-    H, W = sc.views[v].height, sc.views[v].width
+    cfg = oracle.Config(tile_w=16, tile_h=16)
     rng = np.random.default_rng(seed)
-    pix = np.sort(rng.choice(H * W, size=min(n_pix, H * W), replace=False)).astype(np.int64)
-    cfg = oracle.Config()
     t0 = time.perf_counter()
-    p = oracle.preprocess_scene_view(sc, v, cfg)
-    t1 = time.perf_counter()
-    oracle.render_pixels(p, pix)
-    t2 = time.perf_counter()
-    g8 = np.zeros((8, H, W))
-    g8.reshape(8, -1)[:, pix] = rng.normal(size=(8, pix.size))
-    off, cnt = sc.view_ranges()[v]
-    sl = slice(off, off + cnt)
-    oracle.render_bwd(sc.means[sl], sc.scales[sl], sc.quats[sl], p, g8, pix=pix)
-    t3 = time.perf_counter()
-    scale = (H * W) / pix.size
-    per_view = (t1 - t0) + (t3 - t1) * scale
-    desc = (f"view 0 of the workload: oracle preprocess of all {cnt} surfels, forward + reverse at "
-            f"{pix.size} random pixels of {H}x{W}, scaled to the full image (measured {t3 - t0:.1f} s)")
-    return per_view, desc, t3 - t0
+    for v in views:
+        H, W = sc.views[v].height, sc.views[v].width
+        p = oracle.preprocess_scene_view(sc, v, cfg)
+        oracle.render(p)
+        off, cnt = sc.view_ranges()[v]
+        sl = slice(off, off + cnt)
+        oracle.render_bwd(sc.means[sl], sc.scales[sl], sc.quats[sl], p, rng.normal(size=(8, H, W)))
+    wall = time.perf_counter() - t0
+    desc = (f"views {list(views)} of the workload, each in full: oracle preprocess of the view's surfels, forward "
+            f"and reverse pass at every pixel, chain rule (measured {wall:.1f} s on {_omp_threads()} threads)")
+    return wall / len(views), desc, wall
 
 
 def _omp_threads() -> int:
@@ -177,10 +170,10 @@ def run_reference(args, wl_desc, make):
     if rank != 0:
         return
     sc = make(0)
-    n_pix = args.ref_pixels
     times = []
     for i in range(args.warmup + args.steps):
-        per_view, desc, wall = oracle_sample(sc, n_pix, seed=i)
+        # one step: one whole view of the workload (views in turn)
+        per_view, desc, wall = oracle_views(sc, [i % len(sc.views)], seed=i)
         if i >= args.warmup:
             times.append(per_view)
     per_view = float(np.mean(times))
@@ -269,8 +262,7 @@ def main():
     ap.add_argument("--bwd-chunk", type=int, default=None, help="chunk of the backward pass (default: --chunk)")
     ap.add_argument("--plain-steps", type=int, default=2, help="steps of the per-view plain-launch baseline (0=skip)")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-pixels", type=int, default=98304, help="pixels of the oracle CPU-baseline sample (about 10-20 s)")
-    ap.add_argument("--ref-pixels", type=int, default=4096)
+    ap.add_argument("--cpu-views", type=int, default=4, help="whole views the oracle CPU baseline renders (~3 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-json", default=None, help="ncu DRAM-byte summary for the roofline kernel")
     ap.add_argument("--no-maintenance", action="store_true", help="skip timing the map-maintenance kernels")
@@ -536,7 +528,7 @@ def main():
     # ---- CPU baseline (the oracle, host cores, bounded sample) -----------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_view, desc, _ = oracle_sample(sc, args.cpu_pixels)
+        per_view, desc, _ = oracle_views(sc, list(range(min(args.cpu_views, len(sc.views)))))
         cpu = {"value": 1.0 / per_view, "unit": "views/s", "cores": _omp_threads(), "kind": "oracle",
                "sample": desc}
 
