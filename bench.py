@@ -194,6 +194,39 @@ def run_reference(args, wl_desc, make):
 # ---------------------------------------------------------------------------
 # the CUDA path
 # ---------------------------------------------------------------------------
+STAGE_SOURCE = {"render_bwd": "render.cu", "render_fwd": "render.cu", "preprocess": "preprocess.cu",
+                "preprocess_bwd": "preprocess.cu", "bin_sort": "binsort.cu"}
+
+
+def _recorded_traffic(workload: str, stage: str, cfg):
+    """DRAM bytes per launch of the stage's kernel from the ncu capture
+    recorded in profiles/traffic_<workload>.txt, if it was taken on the
+    current kernel source (sha256 of its .cu file) and launch shape; else
+    None."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        line = line.strip()
+        if line and not line.startswith("#") and " " in line:
+            k, v = line.split(None, 1)
+            rec[k] = v
+    src = os.path.join(ROOT, "paper_2604_03092_gb300", "csrc", STAGE_SOURCE.get(stage, ""))
+    if rec.get("stage") != stage or not os.path.isfile(src):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != rec.get("source_sha256"):
+        return None
+    shape = f"{cfg.tile_w}x{cfg.tile_h}/{cfg.chunk}/{cfg.bwd_chunk or cfg.chunk}"
+    if rec.get("launch_shape") != shape:
+        return None
+    try:
+        return int(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _time_maintenance(rast, params, sc, out, dev, hbm_gbs, reps: int = 5):
     """CUDA-event times of the map-maintenance kernels on this workload:
     error attribution over all views (after a forward), the accumulation
@@ -264,7 +297,6 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-views", type=int, default=4, help="whole views the oracle CPU baseline renders (~3 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--traffic-json", default=None, help="ncu DRAM-byte summary for the roofline kernel")
     ap.add_argument("--no-maintenance", action="store_true", help="skip timing the map-maintenance kernels")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -508,12 +540,7 @@ def main():
         else:
             stage_frac[s] = {"bound": "alu", "achieved_tflops": a_ / t_ / 1e12, "frac": a_ / t_ / 1e12 / alu_peak,
                              "ms": stage_ms[s]}
-    traffic = None
-    if args.traffic_json and os.path.exists(args.traffic_json):
-        try:
-            traffic = json.load(open(args.traffic_json)).get(dom)
-        except Exception:
-            traffic = None
+    traffic = _recorded_traffic(args.workload, dom, cfg)
     if bound == "hbm":
         achieved = amount / sec / 1e9
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

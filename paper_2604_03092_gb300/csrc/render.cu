@@ -315,7 +315,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
           C0 = __fmaf_rn(w, col.x, C0);
           C1 = __fmaf_rn(w, col.y, C1);
           C2 = __fmaf_rn(w, col.z, C2);
-          D = __fmaf_rn(w, pair_depth(e, col.w, S.rec.q[j].z, P.depth_ray), D);
+          float zp = col.w;
+          if (P.depth_ray) zp = pair_depth(e, col.w, S.rec.q[j].z, 1);
+          D = __fmaf_rn(w, zp, D);
           N0 = __fmaf_rn(w, nrm.x, N0);
           N1 = __fmaf_rn(w, nrm.y, N1);
           N2 = __fmaf_rn(w, nrm.z, N2);
