@@ -24,9 +24,12 @@ CANDIDATES: List[Candidate] = [(16, 16, 256, 256), (16, 16, 128, 128), (16, 16, 
                                (8, 8, 128, 128), (8, 8, 128, 64), (8, 8, 256, 64), (32, 8, 256, 256),
                                (32, 8, 128, 128)]
 
-# Best launch shapes measured on GB300 (forward + backward step time), by bucket:
-# 512x384 views, ~32 surfels per pixel per view (32-keyframe submaps).
-SHIPPED: Dict[str, Candidate] = {"img18_dens5": (8, 8, 128, 64)}
+# Best launch shapes measured on GB300 (forward + backward step time over the
+# candidates above), by bucket: one 512x384 keyframe seen from 8 views
+# (img18_dens0), 64 uneven submaps at 320x240..640x480 (img18_dens1), 8- and
+# 32-keyframe submaps at 512x384 (img18_dens3, img18_dens5).
+SHIPPED: Dict[str, Candidate] = {"img18_dens0": (8, 8, 128, 64), "img18_dens1": (8, 8, 128, 64),
+                                 "img18_dens3": (8, 8, 128, 64), "img18_dens5": (8, 8, 128, 64)}
 
 
 def _candidate(x) -> Candidate:
