@@ -543,6 +543,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
   uint8_t* own = S.own[wid];
   // a failed binning (instance capacity exceeded) leaves no valid lists
   if (A.hdr->status != 0) return;
+  const bool want_n = A.d_normal != nullptr;  // normal terms only when their gradient is asked for
   // The pixel at tile-local (x, y) is laid out by warp (x + 3y) mod NW -- a
   // diagonal interleave, so every warp's 32 pixels spread over the whole tile
   // and the warps' loads match -- as that warp's pixel number
@@ -690,11 +691,14 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         }
         const float Tb = tq.x * x;
         const float w = kept ? alpha * Tb : 0.f;
-        const float4 col = S.rec.col[j], nrm = S.rec.n[j];
+        const float4 col = S.rec.col[j];
         const float4 qj = S.rec.q[j];
         const float zp = pair_depth(e, col.w, qj.z, P.depth_ray);
-        const float f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, fmaf(u0.w, zp,
-                        fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, u1.z * nrm.z))))));
+        float f = fmaf(u0.x, col.x, fmaf(u0.y, col.y, fmaf(u0.z, col.z, u0.w * zp)));
+        if (want_n) {
+          const float4 nrm = S.rec.n[j];
+          f = fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, fmaf(u1.z, nrm.z, f)));
+        }
         const float wf = w * f;
         // segmented prefix sum: the sum over entries behind this one
         float sum = wf;
@@ -715,8 +719,10 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           // zero terms (clamped alpha, low-pass pairs) skip their atomic
           float* sg = S.grad + j * SGRAD_STRIDE;
 #pragma unroll
-          for (int q = 0; q < 16; q++)
+          for (int q = 0; q < 16; q++) {
+            if (!want_n && q >= G_NX && q <= G_NZ) continue;  // no normal gradient requested
             if (g[q] != 0.f) atomicAdd(sg + q, g[q]);
+          }
           if (gz != 0.f) atomicAdd(sg + 16, gz);
         }
         __syncwarp();

@@ -315,9 +315,15 @@ def test_capacity_overflow_with_surfel_offset_skips_stale_lists():
 # gradients
 # --------------------------------------------------------------------------
 
-def _check_backward(sc, cfg, seed=0, tol=GRAD_REL_L2):
+def _check_backward(sc, cfg, seed=0, tol=GRAD_REL_L2, drop=()):
     rast, params, im = gpu_forward(sc, cfg)
     d_dev, d_views = upstream(rast, seed)
+    # outputs whose upstream gradient is not given (None on the library side, zero for the oracle)
+    chans = {0: (0, 3), 1: (3, 4), 2: (4, 7), 3: (7, 8)}
+    d_dev = tuple(None if k in drop else t for k, t in enumerate(d_dev))
+    for g in d_views:
+        for k in drop:
+            g[chans[k][0]:chans[k][1]] = 0.0
     grads = rast.backward(*params, d_dev)
     torch.cuda.synchronize()
     ocfg = oracle_cfg(cfg)
@@ -360,6 +366,13 @@ def test_backward_ray_depth(seed):
     sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=20 + seed, n_views=2,
                              scale_range=(0.03, 0.2))
     _check_backward(sc, RasterConfig(depth_ray=True, bg=(0.2, 0.1, 0.3)), seed=seed)
+
+
+def test_backward_without_normal_and_alpha_gradients():
+    # the refinement loss uses colour and depth only: the normal and alpha
+    # upstream gradients are absent and the kernel skips their terms
+    sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=31, n_views=2)
+    _check_backward(sc, RasterConfig(), seed=5, drop=(2, 3))
 
 
 def test_backward_keyframe_crop():
