@@ -191,11 +191,16 @@ int splat2d_preprocess(const splat2d_config* cfg, const splat2d_problem* prob, c
 /*
  * Tile binning and sort: every visible (view, surfel) pair emits one
  * instance per tile of its rect, key = (global tile) << 32 | FP32 depth bits,
- * value = surfel index; a device LSD radix sort orders them by key, stable
- * (equal keys keep ascending surfel index); then each tile's [start, end)
- * range is found.  If the instances exceed instance_capacity the device
- * status becomes SPLAT2D_ERR_CAPACITY with the needed count and nothing is
- * rendered; re-run with a larger capacity.
+ * value = surfel index, and the instances are put in key order, ties in
+ * ascending surfel index (the order of a stable sort of the instances
+ * emitted in surfel order).  The tile index is taken as the most significant
+ * digit -- a counting pass gives each tile's [start, end) range and a
+ * scatter fills per-tile buckets -- and each bucket is then sorted by its
+ * depth bits with a radix sort in shared memory.  Follows splat2d_preprocess
+ * on the same workspace.  If the instances exceed instance_capacity the
+ * device status becomes SPLAT2D_ERR_CAPACITY with the needed count and
+ * every later kernel of the iteration does nothing; re-run with a larger
+ * capacity.
  */
 int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
                      splat2d_stream stream);
