@@ -247,7 +247,7 @@ __device__ __forceinline__ uint32_t project_one(const PreArgs& A, const DView& v
   return ntx * nty;
 }
 
-__global__ void __launch_bounds__(256) k_preprocess(const PreArgs A) {
+__global__ void __launch_bounds__(256, 3) k_preprocess(const PreArgs A) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long vis = 0;
   for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < A.n_work; w += stride) {
@@ -322,7 +322,7 @@ struct PreBwdArgs {
 
 constexpr int kPoseSlots = 64;  // per-block pose accumulators (views)
 
-__global__ void __launch_bounds__(256) k_preprocess_bwd(const PreBwdArgs A) {
+__global__ void __launch_bounds__(256, 4) k_preprocess_bwd(const PreBwdArgs A) {
   __shared__ float s_pose[kPoseSlots][6];
   __shared__ int s_vfirst;
   // a failed binning (instance capacity exceeded): nothing was accumulated
