@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
   const int lane = threadIdx.x & 31;
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // this thread's records only increase: follow the owning view forward
+  int v = find_view_by_record(A.views, A.V, min64((int64_t)blockIdx.x * blockDim.x + threadIdx.x, A.R - 1));
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += stride) {
     const int64_t r = r0 + threadIdx.x;
     const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
@@ -61,7 +63,7 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
     int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
     uint64_t comp = 0;
     if (nt) {
-      const int v = find_view_by_record(A.views, A.V, r);
+      while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
       const DView& vw = A.views[v];
       const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
       const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
