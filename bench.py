@@ -541,6 +541,11 @@ def main():
         else:
             stage_frac[s] = {"bound": "alu", "achieved_tflops": a_ / t_ / 1e12, "frac": a_ / t_ / 1e12 / alu_peak,
                              "ms": stage_ms[s]}
+    # composite fraction: the time the stages would take at their bounds
+    # (algorithmic work / peak) over the time they took
+    t_ideal = sum((work[s_][1] / (peaks["hbm_gbs"] * 1e9)) if work[s_][0] == "hbm"
+                  else (work[s_][1] / (alu_peak * 1e12)) for s_ in stages)
+    composite = t_ideal / (sum(stage_ms.values()) / 1e3)
     traffic = _recorded_traffic(args.workload, dom, cfg)
     if bound == "hbm":
         achieved = amount / sec / 1e9
@@ -571,7 +576,7 @@ def main():
                        "bwd_chunk": cfg.bwd_chunk or cfg.chunk, "fwd_tail": cfg.fwd_tail, "instances": n_inst,
                        "visible_pairs": n_vis, "l2": "inputs larger than L2 (records + instances > 129 MB)",
                        "parallelism": f"{world} independent submap(s), one per GPU"},
-            "stages_ms": stage_ms, "stage_roofline": stage_frac,
+            "stages_ms": stage_ms, "stage_roofline": stage_frac, "composite_roofline_frac": composite,
             "roofline": roof, "clocks": clocks,
             "graph_views_per_s": graph_vps, "plain_per_view_views_per_s": plain_vps,
             "e2e": {"value": e2e_vps, "unit": "views/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
