@@ -68,7 +68,8 @@ enum {
   SPLAT2D_ERR_CUDA = -3,               /* a CUDA launch or copy failed */
   SPLAT2D_ERR_CAPACITY = -4,           /* device: more tile instances than instance_capacity */
   SPLAT2D_ERR_TIMEOUT = -5,            /* device: a bounded wait gave up */
-  SPLAT2D_ERR_NO_DEVICE = -6
+  SPLAT2D_ERR_NO_DEVICE = -6,
+  SPLAT2D_ERR_BOUNDS = -7              /* device, checked builds only: an index check failed and the access was skipped */
 };
 
 /* One camera and the surfel range it renders. */

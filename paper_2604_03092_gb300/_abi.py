@@ -17,6 +17,7 @@ ERR_CUDA = -3
 ERR_CAPACITY = -4
 ERR_TIMEOUT = -5
 ERR_NO_DEVICE = -6
+ERR_BOUNDS = -7
 FLAG_NO_STATS = 1
 FLAG_DEPTH_RAY = 2
 SORT_NOALLOC_MAX_PAIRS = 1 << 20

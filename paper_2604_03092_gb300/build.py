@@ -19,6 +19,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libsplat2d.so")
+# SPLAT2D_CHECKS=1 selects the checked build: every kernel index check
+# compiled in (a failed check sets SPLAT2D_ERR_BOUNDS in the status word and
+# skips the access), built into its own library file.
+CHECKED = os.environ.get("SPLAT2D_CHECKS", "0") not in ("", "0")
+if CHECKED:
+    LIB = os.path.join(LIBDIR, "libsplat2d_checks.so")
 SOURCES = ["preprocess.cu", "binsort.cu", "render.cu", "fusion.cu", "api.cu", "sort_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -51,12 +57,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     nvcc = _nvcc()
     os.makedirs(LIBDIR, exist_ok=True)
-    objdir = os.path.join(LIBDIR, "obj")
+    objdir = os.path.join(LIBDIR, "obj_checks" if CHECKED else "obj")
     os.makedirs(objdir, exist_ok=True)
     procs = []
     for src in SOURCES:
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *(["-DS2D_CHECKS"] if CHECKED else []), "-I", INCLUDE, "-c",
+               os.path.join(CSRC, src), "-o", obj]
         if ptxas_info:
             cmd += ["-Xptxas", "-v"]
         procs.append((src, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))

@@ -463,6 +463,7 @@ const char* splat2d_strerror(int code) {
     case SPLAT2D_ERR_CAPACITY: return "instance capacity exceeded";
     case SPLAT2D_ERR_TIMEOUT: return "bounded wait timed out";
     case SPLAT2D_ERR_NO_DEVICE: return "no CUDA device";
+    case SPLAT2D_ERR_BOUNDS: return "index check failed (checked build)";
     default: return "unknown status";
   }
 }

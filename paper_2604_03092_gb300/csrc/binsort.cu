@@ -43,7 +43,8 @@ struct TileBinArgs {
   int32_t tile_w, tile_h;
   uint32_t* counts;  // per tile; the scan turns them into scatter cursors
   unsigned long long* bucket;
-  const Header* hdr;
+  int64_t cap;       // instance capacity (bucket length)
+  Header* hdr;
 };
 
 // Visit every (record, tile) instance; warp lanes hold consecutive records and
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
         uint32_t base = 0;
         if (lead) base = atomicAdd(A.counts + t, run);
         base = __shfl_sync(0xffffffffu, base, leader & 31);
-        if (has) A.bucket[base + (uint32_t)(lane - leader)] = comp;
+        if (has && s2d_check((int64_t)base + (lane - leader) < A.cap, A.hdr)) A.bucket[base + (uint32_t)(lane - leader)] = comp;
       }
     }
   }
@@ -517,7 +518,8 @@ struct SegArgs {
   unsigned long long* scratch;  // ping-pong space for the oversized buckets (same indexing as bucket)
   uint64_t* keys;               // out: (tile << 32) | depth bits
   uint32_t* vals;               // out: surfel index
-  const Header* hdr;
+  Header* hdr;
+  int64_t cap;                  // instance capacity
   const uint32_t* list;         // this class's tiles
   const uint32_t* list_count;   // their number
   uint32_t* queue;              // this class's work counter
@@ -553,6 +555,7 @@ __global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 2 : 1) k_tile_sort
     if (q >= n_tiles) break;
     const uint32_t t = A.list[q];
     const uint2 rg = A.ranges[t];
+    if (!s2d_check(rg.x <= rg.y && (int64_t)rg.y <= A.cap, A.hdr)) continue;
     const int n = (int)(rg.y - rg.x);
     const unsigned long long* res;
     if (!LAST || n <= C::CAP) {
@@ -604,6 +607,7 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   A.tile_h = P.tile_h;
   A.counts = counts;
   A.bucket = reinterpret_cast<unsigned long long*>(ws + L.keys1);
+  A.cap = L.cap;
   A.hdr = hdr;
   const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 16);
   k_tile_pass<false><<<grid, 256, 0, st>>>(A);
@@ -623,6 +627,7 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   S.keys = reinterpret_cast<uint64_t*>(ws + L.keys0);
   S.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
   S.hdr = hdr;
+  S.cap = L.cap;
   static_assert(SegClass<8, 4>::CAP == SORT_CLASS_BOUND[0] && SegClass<16, 8>::CAP == SORT_CLASS_BOUND[1] &&
                     SegClass<16, 12>::CAP == SORT_CLASS_BOUND[2] && SegClass<32, 12>::CAP == SORT_CLASS_BOUND[3],
                 "class capacities match the class bounds");

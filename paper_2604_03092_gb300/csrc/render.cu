@@ -122,6 +122,7 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
                                             SRecs<CHUNK>& s_rec, uint32_t* s_idx) {
   for (int j = threadIdx.x; j < count; j += NT) {
     const uint32_t s = __ldg(A.vals + base + j);
+    if (!s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) continue;
     const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
     unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j);
     if (s_idx) s_idx[j] = (uint32_t)rec;
@@ -845,7 +846,8 @@ __global__ void __launch_bounds__(TW* TH) k_max_error(const RenderArgs A, const 
       __syncthreads();
       for (int j = threadIdx.x; j < count; j += NT) {
         const uint32_t m = S.emax[j];
-        if (m) atomicMax(max_err + __ldg(A.vals + lo + j), m);
+        const uint32_t sj = __ldg(A.vals + lo + j);
+        if (m && s2d_check((int64_t)sj >= vw.soff && (int64_t)sj < vw.soff + vw.scnt, A.hdr)) atomicMax(max_err + sj, m);
       }
       __syncthreads();
     }

@@ -246,6 +246,19 @@ __device__ __forceinline__ int find_group(const DGroup* groups, int G, int64_t w
   return lo;
 }
 
+// Index checks of the checked build (compiled with S2D_CHECKS): a failed
+// check records SPLAT2D_ERR_BOUNDS in the status word (unless an earlier
+// status is there) and the caller skips the access; nothing traps.  In the
+// normal build the checks compile away.
+#ifdef S2D_CHECKS
+__device__ __forceinline__ bool s2d_check(bool ok, Header* hdr) {
+  if (!ok) atomicCAS(reinterpret_cast<int*>(&hdr->status), 0, (int)SPLAT2D_ERR_BOUNDS);
+  return ok;
+}
+#else
+__device__ __forceinline__ bool s2d_check(bool ok, Header*) { return true; }
+#endif
+
 #endif  // __CUDACC__
 
 }  // namespace s2d
