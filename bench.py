@@ -582,7 +582,7 @@ def main():
             "e2e": {"value": e2e_vps, "unit": "views/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "pairs": {k: st[k] for k in ("fwd_pairs_evaluated", "fwd_pairs_blended", "bwd_pairs_evaluated",
-                                         "bwd_pairs_blended")},
+                                         "bwd_pairs_blended", "bwd_terms_outside")},
             "cpu_baseline": cpu,
             "map_maintenance": maint,
         }

@@ -164,7 +164,8 @@ typedef struct {
   int64_t bwd_pairs_evaluated; /* (pixel, surfel) pairs the reverse pass recomputed */
   int64_t bwd_pairs_blended;   /* ... of which carried gradient */
   int64_t sort_passes;         /* radix passes run */
-  int64_t reserved[7];
+  int64_t bwd_terms_outside;   /* gradient terms outside their chunk's fixed-point range, added in float */
+  int64_t reserved[6];
 } splat2d_stats_t;
 
 /* Fill `cfg` with the defaults above. */

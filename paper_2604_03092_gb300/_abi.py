@@ -59,7 +59,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("status", c_int64), ("needed_capacity", c_int64), ("n_instances", c_int64),
                 ("n_visible", c_int64), ("fwd_pairs_evaluated", c_int64), ("fwd_pairs_blended", c_int64),
                 ("bwd_pairs_evaluated", c_int64), ("bwd_pairs_blended", c_int64), ("sort_passes", c_int64),
-                ("reserved", c_int64 * 7)]
+                ("bwd_terms_outside", c_int64), ("reserved", c_int64 * 6)]
 
 
 class Layout(ctypes.Structure):

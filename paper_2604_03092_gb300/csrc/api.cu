@@ -412,6 +412,7 @@ int splat2d_stats(const void* ws, splat2d_stats_t* out, splat2d_stream stream) {
   out->fwd_pairs_blended = (int64_t)h.stat[STAT_FWD_BLEND];
   out->bwd_pairs_evaluated = (int64_t)h.stat[STAT_BWD_EVAL];
   out->bwd_pairs_blended = (int64_t)h.stat[STAT_BWD_BLEND];
+  out->bwd_terms_outside = (int64_t)h.stat[STAT_BWD_OUTSIDE];
   return h.status;
 }
 

@@ -449,6 +449,29 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
 
 constexpr int SGRAD_STRIDE = 17;
 
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
+// Per-entry gradient sums of a chunk in shared memory are kept in fixed point
+// (integer shared atomics run at several times the rate of float ones).  Each
+// quantity q has, per tile and chunk, a power-of-two scale s_q: a term t is
+// added as round(t s_q) when |t s_q| < 2^22 (so a slot, which takes one term
+// per pixel of the tile, stays below 2^30), and otherwise straight to the
+// gradient record in global memory as a float, so no term is ever clipped.
+// The scale comes from the previous chunk of the same tile: 2^FIX_BITS over
+// the geometric mean of its nonzero per-entry sums, or, where it had none,
+// over the largest term that went to global memory.  A tile's first chunk has
+// no previous one and accumulates in float; until a quantity has a scale, its
+// terms go to global memory.  Scales are exact powers of two, so the only
+// rounding is that of each term to the nearest multiple of 1 / s_q: relative
+// to the typical entry sum of the tile, 2^-FIX_BITS.
+constexpr int FIX_BITS = 15;
+constexpr float FIX_LIMIT = 4194304.f;  // 2^22
+constexpr float FIX_MAGIC = 12582912.f;  // 1.5 * 2^23: adding it rounds |u| < 2^22 to an integer in the low bits
+constexpr int FIX_MAGIC_BITS = 0x4B400000;
+
 // Gradient of one kept (pixel, entry) pair w.r.t. the 16 stored record
 // quantities (G_* order) and the depth; `da` is dL/dalpha.  Written without
 // branches (selects only): the clamped and the low-pass cases zero the terms
@@ -513,6 +536,10 @@ struct BwdSmem {
   uint16_t pcnt[NT][CHUNK / 32];   // per pixel: set bits in its mask words >= w (from the deepest word)
   float4 up[NT][2];                // per pixel: dC0 dC1 dC2 dD | dN0 dN1 dN2 dA*T_final
   float2 tq[NT];                   // per pixel: (T in front of the deepest unprocessed entry, Q behind it)
+  uint32_t gexp[(SGRAD_STRIDE + 1) / 2];  // per quantity, 16 bits: the upper half of this chunk's scale (+inf: none)
+  float ginv[SGRAD_STRIDE];        // per quantity: inverse of the scale (0: none)
+  uint32_t estat[SGRAD_STRIDE];    // per quantity: (sum of biased exponents of nonzero entry sums) << 10 | their number
+  uint32_t ofl[SGRAD_STRIDE];      // per quantity: largest biased exponent of a term added outside the slots
   uint8_t own[NT / 32][32];        // per warp and step: lane of the pixel whose run starts at each position
   int item;
   uint32_t top;
@@ -540,7 +567,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t le_mask = (2u << lane) - 1u;  // lanes <= this lane
   const RastParams& P = A.P;
-  uint32_t n_eval = 0, n_blend = 0;
+  uint32_t n_eval = 0, n_blend = 0, n_outside = 0;
   uint8_t* own = S.own[wid];
   // a failed binning (instance capacity exceeded) leaves no valid lists
   if (A.hdr->status != 0) return;
@@ -552,6 +579,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
   // warp * 32 + number, so one warp's pixels sit in consecutive slots.
   constexpr int PR = TW / NW;  // pixels per row of one warp
   static_assert(TW % NW == 0 && PR * TH == 32, "each warp lays out 32 pixels");
+  static_assert(NT <= 256, "a fixed-point slot takes one term below 2^22 per pixel and must stay below 2^30");
   const int lx = (wid % WX) * 8 + (lane & 7), ly = (wid / WX) * 4 + (lane >> 3);
   const int myslot = ((lx + 3 * ly) % NW) * 32 + ly * PR + lx / NW;  // slot of this thread's own pixel
   const int mine = wid * 32 + lane;                                  // slot of the pixel this lane lays out
@@ -573,6 +601,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     const int64_t HW = (int64_t)vw.W * vw.H;
     uint32_t my_last = range.x;
     float T = 1.f, Q = 0.f;
+    bool fixed = false;  // a tile's first chunk accumulates in float, every later one in fixed point
     {
       float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
       if (inside) {
@@ -595,6 +624,12 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       S.up[myslot][1] = u1;
     }
     if (threadIdx.x == 0) S.top = range.x;
+    if (threadIdx.x < (SGRAD_STRIDE + 1) / 2) S.gexp[threadIdx.x] = 0x7f807f80u;
+    if (threadIdx.x < SGRAD_STRIDE) {
+      S.ginv[threadIdx.x] = 0.f;
+      S.estat[threadIdx.x] = 0u;
+      S.ofl[threadIdx.x] = 0u;
+    }
     __syncthreads();
     if (my_last > range.x) atomicMax(&S.top, my_last);
     __syncthreads();
@@ -640,7 +675,13 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       }
       const uint32_t myoff = incl - cnt;
       const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      // the chunk's steps, compiled once per way of accumulating the sums
+      auto steps = [&](auto fixed_tag) {
+      constexpr bool FIXED = decltype(fixed_tag)::value;
       int carry = 0;  // lane of the pixel whose run reaches the previous step's last position
+      uint32_t gexp[(SGRAD_STRIDE + 1) / 2];  // this chunk's scales, in registers
+#pragma unroll
+      for (int w = 0; w < (SGRAD_STRIDE + 1) / 2; w++) gexp[w] = FIXED ? S.gexp[w] : 0u;
       for (uint32_t base = 0; base < total; base += 32) {
         const bool starts_here = cnt > 0 && myoff >= base && myoff < base + 32;
         if (starts_here) own[myoff - base] = (uint8_t)lane;
@@ -720,40 +761,89 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           // zero terms (clamped alpha, low-pass pairs) skip their atomic
           float* sg = S.grad + j * SGRAD_STRIDE;
 #pragma unroll
-          for (int q = 0; q < 16; q++) {
+          for (int q = 0; q < SGRAD_STRIDE; q++) {
             if (!want_n && q >= G_NX && q <= G_NZ) continue;  // no normal gradient requested
-            if (g[q] != 0.f) atomicAdd(sg + q, g[q]);
+            const float t = q < 16 ? g[q] : gz;
+            if constexpr (FIXED) {
+              // no scale yet (+inf) makes u infinite or NaN: the term goes outside
+              const uint32_t w2 = gexp[q >> 1];
+              const float u = t * __uint_as_float((q & 1) ? (w2 & 0xffff0000u) : (w2 << 16));
+              const bool in = fabsf(u) < FIX_LIMIT;
+              if (in) atomicAdd(reinterpret_cast<int*>(sg + q), __float_as_int(__fadd_rn(u, FIX_MAGIC)) - FIX_MAGIC_BITS);
+              else if (t != 0.f) {  // outside this chunk's range (or not finite): add it exactly
+                atomicAdd(A.rgrad + (int64_t)S.idx[j] * GRAD_F + q, t);
+                atomicMax(&S.ofl[q], (__float_as_uint(t) >> 23) & 0xffu);
+                n_outside++;
+              }
+            } else {
+              if (t != 0.f) atomicAdd(sg + q, t);
+            }
           }
-          if (gz != 0.f) atomicAdd(sg + 16, gz);
         }
         __syncwarp();
         if (end) S.tq[ps] = make_float2(Tb, tq.y + sum);
         __syncwarp();
       }
+      };
+      if (fixed)
+        steps(BoolTag<true>{});
+      else
+        steps(BoolTag<false>{});
       __syncthreads();
       if (act) {
         const float2 tq = S.tq[myslot];
         T = tq.x;
         Q = tq.y;
       }
-      // flush this chunk's per-entry sums: one set of vector atomics per entry
-      for (int jj = threadIdx.x; jj < count; jj += NT) {
-        float* sg = S.grad + jj * SGRAD_STRIDE;
+      // flush this chunk's per-entry sums (decoded from fixed point where the
+      // chunk used it): one set of vector atomics per entry; then gather the
+      // exponent statistics the next chunk's scales come from
+      for (int j0 = 0; j0 < count; j0 += NT) {
+        const int jj = j0 + (int)threadIdx.x;
+        const bool valid = jj < count;
+        uint32_t* sg = reinterpret_cast<uint32_t*>(S.grad) + (valid ? jj : 0) * SGRAD_STRIDE;
+        float v[SGRAD_STRIDE];
         float acc = 0.f;
 #pragma unroll
-        for (int q = 0; q < 17; q++) acc += fabsf(sg[q]);
-        if (acc != 0.f) {
+        for (int q = 0; q < SGRAD_STRIDE; q++) {
+          const uint32_t raw = valid ? sg[q] : 0u;
+          v[q] = fixed ? (float)(int)raw * S.ginv[q] : __uint_as_float(raw);
+          acc += fabsf(v[q]);
+        }
+        if (valid && acc != 0.f) {
           float* dst = A.rgrad + (int64_t)S.idx[jj] * GRAD_F;
-          red_add_v4(dst + 0, sg[0], sg[1], sg[2], sg[3]);
-          red_add_v4(dst + 4, sg[4], sg[5], sg[6], sg[7]);
-          red_add_v4(dst + 8, sg[8], sg[9], sg[10], sg[11]);
-          red_add_v4(dst + 12, sg[12], sg[13], sg[14], sg[15]);
-          atomicAdd(dst + 16, sg[16]);
+          red_add_v4(dst + 0, v[0], v[1], v[2], v[3]);
+          red_add_v4(dst + 4, v[4], v[5], v[6], v[7]);
+          red_add_v4(dst + 8, v[8], v[9], v[10], v[11]);
+          red_add_v4(dst + 12, v[12], v[13], v[14], v[15]);
+          atomicAdd(dst + 16, v[16]);
 #pragma unroll
-          for (int q = 0; q < 17; q++) sg[q] = 0.f;
+          for (int q = 0; q < SGRAD_STRIDE; q++) sg[q] = 0u;
+        }
+#pragma unroll
+        for (int q = 0; q < SGRAD_STRIDE; q++) {
+          const uint32_t e = v[q] != 0.f ? ((__float_as_uint(v[q]) >> 23) & 0xffu) << 10 | 1u : 0u;
+          const uint32_t es = __reduce_add_sync(0xffffffffu, e);
+          if (lane == 0 && es) atomicAdd(&S.estat[q], es);
         }
       }
       __syncthreads();
+      // next chunk's scales: 2^(FIX_BITS - e) for the mean unbiased exponent e
+      // of this chunk's nonzero sums (or, with none, for the largest term that
+      // went outside); a quantity with neither keeps its scale
+      if (threadIdx.x < SGRAD_STRIDE) {
+        const uint32_t st = S.estat[threadIdx.x], c = st & 1023u, of = S.ofl[threadIdx.x];
+        const int m = c ? (int)((st >> 10) / c) : (of ? (int)of : -1);
+        if (m >= 0) {
+          const int es = 254 + FIX_BITS - m, ei = m - FIX_BITS;
+          const bool ok = es >= 1 && es <= 254 && ei >= 1 && ei <= 254;
+          S.ginv[threadIdx.x] = ok ? __uint_as_float((uint32_t)ei << 23) : 0.f;
+          reinterpret_cast<uint16_t*>(S.gexp)[threadIdx.x] = (uint16_t)((ok ? es : 255) << 7);
+        }
+        S.estat[threadIdx.x] = 0u;
+        S.ofl[threadIdx.x] = 0u;
+      }
+      fixed = true;
     }
   }
   if (P.stats) {
@@ -766,6 +856,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       atomicAdd(&A.hdr->stat[STAT_BWD_EVAL], a);
       atomicAdd(&A.hdr->stat[STAT_BWD_BLEND], bb);
     }
+    unsigned long long o = n_outside;
+    for (int sh = 16; sh > 0; sh >>= 1) o += __shfl_xor_sync(0xffffffffu, o, sh);
+    if (lane == 0 && o) atomicAdd(&A.hdr->stat[STAT_BWD_OUTSIDE], o);
   }
 }
 

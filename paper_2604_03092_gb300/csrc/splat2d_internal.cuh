@@ -56,7 +56,7 @@ struct Header {
   uint32_t pad[31];
 };
 static_assert(sizeof(Header) <= 256, "Header layout");
-enum { STAT_FWD_EVAL = 0, STAT_FWD_BLEND = 1, STAT_BWD_EVAL = 2, STAT_BWD_BLEND = 3 };
+enum { STAT_FWD_EVAL = 0, STAT_FWD_BLEND = 1, STAT_BWD_EVAL = 2, STAT_BWD_BLEND = 3, STAT_BWD_OUTSIDE = 4 };
 
 // Render record: 80 bytes per visible (view, surfel).  Geometry is stored
 // relative to the projected center c = (cx_hi + cx_lo, cy_hi + cy_lo), kept
