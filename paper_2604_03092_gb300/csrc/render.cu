@@ -460,9 +460,10 @@ struct BoolTag {
 // added as round(t s_q) when |t s_q| < 2^22 (so a slot, which takes one term
 // per pixel of the tile, stays below 2^30), and otherwise straight to the
 // gradient record in global memory as a float, so no term is ever clipped.
-// The scale comes from the previous chunk of the same tile: 2^FIX_BITS over
-// the geometric mean of its nonzero per-entry sums, or, where it had none,
-// over the largest term that went to global memory.  A tile's first chunk has
+// The scale comes from an earlier chunk of the same tile (re-derived after
+// every other chunk): 2^FIX_BITS over the geometric mean of its nonzero
+// per-entry sums, or, where it had none, over the largest term that went to
+// global memory.  A tile's first chunk has
 // no previous one and accumulates in float; until a quantity has a scale, its
 // terms go to global memory.  Scales are exact powers of two, so the only
 // rounding is that of each term to the nearest multiple of 1 / s_q: relative
@@ -602,6 +603,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     uint32_t my_last = range.x;
     float T = 1.f, Q = 0.f;
     bool fixed = false;  // a tile's first chunk accumulates in float, every later one in fixed point
+    bool restat = true;  // the scales are re-derived after every other chunk
     {
       float4 u0 = make_float4(0.f, 0.f, 0.f, 0.f), u1 = u0;
       if (inside) {
@@ -820,18 +822,20 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
 #pragma unroll
           for (int q = 0; q < SGRAD_STRIDE; q++) sg[q] = 0u;
         }
+        if (restat) {
 #pragma unroll
-        for (int q = 0; q < SGRAD_STRIDE; q++) {
-          const uint32_t e = v[q] != 0.f ? ((__float_as_uint(v[q]) >> 23) & 0xffu) << 10 | 1u : 0u;
-          const uint32_t es = __reduce_add_sync(0xffffffffu, e);
-          if (lane == 0 && es) atomicAdd(&S.estat[q], es);
+          for (int q = 0; q < SGRAD_STRIDE; q++) {
+            const uint32_t e = v[q] != 0.f ? ((__float_as_uint(v[q]) >> 23) & 0xffu) << 10 | 1u : 0u;
+            const uint32_t es = __reduce_add_sync(0xffffffffu, e);
+            if (lane == 0 && es) atomicAdd(&S.estat[q], es);
+          }
         }
       }
       __syncthreads();
       // next chunk's scales: 2^(FIX_BITS - e) for the mean unbiased exponent e
       // of this chunk's nonzero sums (or, with none, for the largest term that
       // went outside); a quantity with neither keeps its scale
-      if (threadIdx.x < SGRAD_STRIDE) {
+      if (restat && threadIdx.x < SGRAD_STRIDE) {
         const uint32_t st = S.estat[threadIdx.x], c = st & 1023u, of = S.ofl[threadIdx.x];
         const int m = c ? (int)((st >> 10) / c) : (of ? (int)of : -1);
         if (m >= 0) {
@@ -844,6 +848,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         S.ofl[threadIdx.x] = 0u;
       }
       fixed = true;
+      restat = !restat;
     }
   }
   if (P.stats) {
