@@ -117,15 +117,34 @@ struct RenderArgs {
 };
 
 // Stage entries [base, base + count) of the sorted list into shared memory.
+// Copies entries [base, base + count) of the sorted list's records to shared
+// memory and asks L2 for the records of the chunk processed next
+// ([nbase, nbase + ncount)), so that its copy does not wait on DRAM: the
+// staging is a dependent gather (list entry, then record) and its latency,
+// not bandwidth, is what bounds it.
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                            SRecs<CHUNK>& s_rec, uint32_t* s_idx) {
-  for (int j = threadIdx.x; j < count; j += NT) {
-    const uint32_t s = __ldg(A.vals + base + j);
-    if (!s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) continue;
-    const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
-    unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j);
-    if (s_idx) s_idx[j] = (uint32_t)rec;
+                                            SRecs<CHUNK>& s_rec, uint32_t* s_idx, int64_t nbase, int ncount) {
+  for (int j = threadIdx.x; j < count || j < ncount; j += NT) {
+    uint32_t sn = 0xffffffffu;
+    if (j < ncount) sn = __ldg(A.vals + nbase + j);
+    if (j < count) {
+      const uint32_t s = __ldg(A.vals + base + j);
+      if (s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) {
+        const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
+        unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j);
+        if (s_idx) s_idx[j] = (uint32_t)rec;
+      }
+    }
+    // only records inside the view's range are prefetched, whatever the list holds
+    if (j < ncount && (int64_t)sn >= vw.soff && (int64_t)sn < vw.soff + vw.scnt) {
+      const float4* r = A.records + (vw.rbase + ((int64_t)sn - vw.soff)) * REC_F4;
+      prefetch_l2(r);
+      prefetch_l2(r + REC_F4 - 1);
+    }
   }
 }
 
@@ -286,7 +305,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
         S.nact = 0;
         S.next = 0;
       }
-      stage_chunk<NT, CHUNK>(A, vw, base, count, S.rec, nullptr);
+      stage_chunk<NT, CHUNK>(A, vw, base, count, S.rec, nullptr, base + CHUNK,
+                             (int)max64(min64(CHUNK, (int64_t)range.y - base - CHUNK), 0));
       __syncthreads();
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
@@ -641,7 +661,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int count = (int)(hi - lo);
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
-      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx);
+      const int64_t nlo = max64((int64_t)range.x, lo - CHUNK);  // the chunk in front, processed next
+      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
       __syncthreads();
       // per-pixel masks of this chunk, restricted to the entries below the pixel's last
       const int lim = act ? (int)min64((int64_t)my_last - lo, count) : 0;
@@ -925,7 +946,8 @@ __global__ void __launch_bounds__(TW* TH) k_max_error(const RenderArgs A, const 
     for (int64_t lo = range.x; lo < (int64_t)top; lo += CHUNK) {
       const int count = (int)min64(CHUNK, (int64_t)top - lo);
       const int nwd = (count + 31) >> 5;
-      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, nullptr);
+      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, nullptr, lo + CHUNK,
+                             (int)max64(min64(CHUNK, (int64_t)top - lo - CHUNK), 0));
       for (int j = threadIdx.x; j < count; j += NT) S.emax[j] = 0u;
       __syncthreads();
       const int lim = (int)min64(max64((int64_t)my_last - lo, 0), count);
