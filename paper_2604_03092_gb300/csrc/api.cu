@@ -165,6 +165,9 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->tile_class = take(sizeof(uint32_t) * 4 * (size_t)T);  // one list per bucket-sort size class
   L->tfinal = take(sizeof(float) * P);
   L->last = take(sizeof(uint32_t) * P);
+  // the records in sorted-list order, written by the forward as it stages
+  // them and read back contiguously by the backward
+  L->rcopy = take(sizeof(float4) * REC_F4 * (size_t)L->cap);
   L->total = off;
   return true;
 }

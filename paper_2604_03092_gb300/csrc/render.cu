@@ -40,9 +40,17 @@ struct SRecs {
 };
 
 template <int CHUNK>
-__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRecs<CHUNK>& o, int j) {
+__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRecs<CHUNK>& o, int j,
+                                              float4* __restrict__ copy = nullptr) {
   const float4 f0 = __ldg(rec + 0), f1 = __ldg(rec + 1), f2 = __ldg(rec + 2), f3 = __ldg(rec + 3),
                f4 = __ldg(rec + 4);
+  if (copy) {
+    copy[0] = f0;
+    copy[1] = f1;
+    copy[2] = f2;
+    copy[3] = f3;
+    copy[4] = f4;
+  }
   const float2 lo = unpack_half2_scaled(__float_as_uint(f0.z));
   o.c[j] = make_float4(f0.x, f0.y, lo.x, lo.y);
   o.p[j] = f1;
@@ -101,6 +109,7 @@ struct RenderArgs {
   const uint32_t* order;
   const uint32_t* vals;
   const float4* records;
+  float4* rcopy;  // records in sorted-list order (instance i at i * REC_F4)
   float* rgrad;
   RastParams P;
   Header* hdr;
@@ -127,7 +136,8 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                            SRecs<CHUNK>& s_rec, uint32_t* s_idx, int64_t nbase, int ncount) {
+                                            SRecs<CHUNK>& s_rec, uint32_t* s_idx, int64_t nbase, int ncount,
+                                            bool keep_copy = false) {
   for (int j = threadIdx.x; j < count || j < ncount; j += NT) {
     uint32_t sn = 0xffffffffu;
     if (j < ncount) sn = __ldg(A.vals + nbase + j);
@@ -135,7 +145,7 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
       const uint32_t s = __ldg(A.vals + base + j);
       if (s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) {
         const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
-        unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j);
+        unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j, keep_copy ? A.rcopy + (base + j) * REC_F4 : nullptr);
         if (s_idx) s_idx[j] = (uint32_t)rec;
       }
     }
@@ -146,6 +156,25 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
       prefetch_l2(r + REC_F4 - 1);
     }
   }
+}
+
+// Copies entries [base, base + count) from the sorted-order record copy the
+// forward left (contiguous, so the loads coalesce and wait on nothing), the
+// record index of each entry (for the gradient records) from the list, and
+// asks L2 for the contiguous records of the chunk processed next.
+template <int NT, int CHUNK>
+__device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView& vw, int64_t base, int count,
+                                                SRecs<CHUNK>& s_rec, uint32_t* s_idx, int64_t nbase, int ncount) {
+  for (int j = threadIdx.x; j < count; j += NT) {
+    const uint32_t s = __ldg(A.vals + base + j);
+    if (!s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) continue;
+    unpack_record<CHUNK>(A.rcopy + (base + j) * REC_F4, s_rec, j);
+    s_idx[j] = (uint32_t)(vw.rbase + ((int64_t)s - vw.soff));
+  }
+  // 128-byte lines of the next chunk's records
+  const int64_t b0 = (nbase * REC_F4 * 16) >> 7, b1 = ((nbase + ncount) * REC_F4 * 16 + 127) >> 7;
+  const char* c0 = reinterpret_cast<const char*>(A.rcopy);
+  for (int64_t l = b0 + threadIdx.x; ncount > 0 && l < b1; l += NT) prefetch_l2(c0 + (l << 7));
 }
 
 // Per-lane visit masks.  Each warp owns an 8x4 pixel patch (lane = column
@@ -306,7 +335,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd
         S.next = 0;
       }
       stage_chunk<NT, CHUNK>(A, vw, base, count, S.rec, nullptr, base + CHUNK,
-                             (int)max64(min64(CHUNK, (int64_t)range.y - base - CHUNK), 0));
+                             (int)max64(min64(CHUNK, (int64_t)range.y - base - CHUNK), 0), true);
       __syncthreads();
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
@@ -662,7 +691,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
       const int64_t nlo = max64((int64_t)range.x, lo - CHUNK);  // the chunk in front, processed next
-      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
+      stage_chunk_seq<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
       __syncthreads();
       // per-pixel masks of this chunk, restricted to the entries below the pixel's last
       const int lim = act ? (int)min64((int64_t)my_last - lo, count) : 0;
@@ -986,6 +1015,7 @@ static RenderArgs make_args(const Layout& L, const RastParams& P, char* ws, cons
   A.order = reinterpret_cast<const uint32_t*>(ws + L.tile_order);
   A.vals = vals;
   A.records = reinterpret_cast<const float4*>(ws + L.records);
+  A.rcopy = reinterpret_cast<float4*>(ws + L.rcopy);
   A.rgrad = reinterpret_cast<float*>(ws + L.rgrad);
   A.P = P;
   A.hdr = reinterpret_cast<Header*>(ws + L.header);
