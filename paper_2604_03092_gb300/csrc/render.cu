@@ -44,12 +44,12 @@ __device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SR
                                               float4* __restrict__ copy = nullptr) {
   const float4 f0 = __ldg(rec + 0), f1 = __ldg(rec + 1), f2 = __ldg(rec + 2), f3 = __ldg(rec + 3),
                f4 = __ldg(rec + 4);
-  if (copy) {
-    copy[0] = f0;
-    copy[1] = f1;
-    copy[2] = f2;
-    copy[3] = f3;
-    copy[4] = f4;
+  if (copy) {  // streaming stores: read back only by the backward, long after
+    __stcs(copy + 0, f0);
+    __stcs(copy + 1, f1);
+    __stcs(copy + 2, f2);
+    __stcs(copy + 3, f3);
+    __stcs(copy + 4, f4);
   }
   const float2 lo = unpack_half2_scaled(__float_as_uint(f0.z));
   o.c[j] = make_float4(f0.x, f0.y, lo.x, lo.y);
