@@ -29,7 +29,7 @@ CANDIDATES: List[Candidate] = [(16, 16, 256, 256), (16, 16, 128, 128), (16, 16, 
 # (img18_dens0), 64 uneven submaps at 320x240..640x480 (img18_dens1), 8- and
 # 32-keyframe submaps at 512x384 (img18_dens3, img18_dens5).
 SHIPPED: Dict[str, Candidate] = {"img18_dens0": (8, 8, 128, 64), "img18_dens1": (8, 8, 128, 64),
-                                 "img18_dens3": (8, 8, 128, 64), "img18_dens5": (8, 8, 128, 64)}
+                                 "img18_dens3": (8, 8, 64, 64), "img18_dens5": (8, 8, 64, 64)}
 
 
 def _candidate(x) -> Candidate:

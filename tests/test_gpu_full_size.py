@@ -1,6 +1,6 @@
 """Parity at the full benchmark size: the 32-keyframe submap (6,291,456
 surfels, 32 views at 512x384) in the launch configuration the benchmark
-times (the default 8x8 tiles, 128/64-entry chunks), checked against the
+times (the shipped GB300 launch shape of its bucket), checked against the
 oracle on sampled pixels -- the forward outputs pixel by pixel, and the
 gradients of an upstream gradient that is nonzero only at the sampled
 pixels of one view (so the oracle's sampled reverse pass is the whole
@@ -11,7 +11,7 @@ import torch
 
 import oracle
 from gpu_utils import FWD_ATOL, GRAD_REL_L2, oracle_cfg, rel_l2, to_dev, view_stack
-from paper_2604_03092_gb300 import scenes
+from paper_2604_03092_gb300 import autotune, scenes
 from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -21,7 +21,8 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 def submap():
     sc = scenes.submap_scene(seed=2001, n_keyframes=32)
     assert sc.n == 6_291_456 and len(sc.views) == 32
-    cfg = RasterConfig()
+    tw, th, ch, bch = autotune.SHIPPED[autotune.bucket_key(sc.views, sc.n)]
+    cfg = RasterConfig(tile_w=tw, tile_h=th, chunk=ch, bwd_chunk=bch)
     params = to_dev(sc)
     rast = Rasterizer(sc.views, sc.n, cfg)
     im = rast.forward(*params)
