@@ -297,7 +297,7 @@ struct FwdSmem {
 // warp are still compositing, all warps share them, one pixel at a time.
 
 template <int TW, int TH, int CHUNK>
-__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? 12 : 3) k_render_fwd(const RenderArgs A) {
+__global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 12) : 3) k_render_fwd(const RenderArgs A) {
   constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FwdSmem<NT, CHUNK>& S = *reinterpret_cast<FwdSmem<NT, CHUNK>*>(smem_raw);
