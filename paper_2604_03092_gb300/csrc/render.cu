@@ -35,13 +35,23 @@ struct SRecs {
   float4 p[CHUNK];    // p00 p01 p10 p11
   float4 q[CHUNK];    // p20 p21 p22 opacity
   float4 col[CHUNK];  // r g b z
-  float4 n[CHUNK];    // nx ny nz -
-  int4 rect[CHUNK];   // x0 y0 (x1 - x0) (y1 - y0)
+  float4 n[CHUNK];    // nx ny nz, and in .w the pixel rect clipped to the tile (see pack_tile_rect)
 };
 
+// A record's pixel rect clipped to the tile and made relative to its origin,
+// one byte per bound: x0 | y0 << 8 | x1 << 16 | y1 << 24 (inclusive; an
+// empty clip has x0 > x1).  Tiles are at most 32 pixels wide.
+__device__ __forceinline__ uint32_t pack_tile_rect(int x0, int y0, int x1, int y1, int tx0, int ty0, int tw,
+                                                   int th) {
+  const int a0 = max(x0 - tx0, 0), a1 = min(x1 - tx0, tw - 1);
+  const int b0 = max(y0 - ty0, 0), b1 = min(y1 - ty0, th - 1);
+  if (a0 > a1 || b0 > b1) return 0xffu;  // x0 = 255 > x1 = 0
+  return (uint32_t)a0 | (uint32_t)b0 << 8 | (uint32_t)a1 << 16 | (uint32_t)b1 << 24;
+}
+
 template <int CHUNK>
-__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRecs<CHUNK>& o, int j,
-                                              float4* __restrict__ copy = nullptr) {
+__device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRecs<CHUNK>& o, int j, int tx0,
+                                              int ty0, int tw, int th, float4* __restrict__ copy = nullptr) {
   const float4 f0 = __ldg(rec + 0), f1 = __ldg(rec + 1), f2 = __ldg(rec + 2), f3 = __ldg(rec + 3),
                f4 = __ldg(rec + 4);
   if (copy) {  // streaming stores: read back only by the backward, long after
@@ -56,10 +66,9 @@ __device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SR
   o.p[j] = f1;
   o.q[j] = make_float4(f2.x, f2.y, f2.z, f0.w);
   o.col[j] = make_float4(f2.w, f3.x, f3.y, f4.y);
-  o.n[j] = make_float4(f3.z, f3.w, f4.x, 0.f);
   const uint32_t r0 = __float_as_uint(f4.z), r1 = __float_as_uint(f4.w);
   const int x0 = (int)(r0 & 0xffffu), y0 = (int)(r0 >> 16), x1 = (int)(r1 & 0xffffu), y1 = (int)(r1 >> 16);
-  o.rect[j] = make_int4(x0, y0, x1 - x0, y1 - y0);
+  o.n[j] = make_float4(f3.z, f3.w, f4.x, __uint_as_float(pack_tile_rect(x0, y0, x1, y1, tx0, ty0, tw, th)));
 }
 
 // alpha of one (pixel, record) pair.  Written with explicit round-to-nearest
@@ -97,8 +106,10 @@ __device__ __forceinline__ float pair_depth(const Pair& e, float z, float p22, i
   return (depth_ray && e.obj) ? z * p22 * e.rc : z;
 }
 
-__device__ __forceinline__ bool in_rect(const int4 r, int px, int py) {
-  return (unsigned)(px - r.x) <= (unsigned)r.z && (unsigned)(py - r.y) <= (unsigned)r.w;
+// Whether the tile-relative pixel (lx, ly) lies in a packed clipped rect.
+__device__ __forceinline__ bool in_tile_rect(uint32_t r, int lx, int ly) {
+  return lx >= (int)(r & 0xffu) && ly >= (int)((r >> 8) & 0xffu) && lx <= (int)((r >> 16) & 0xffu) &&
+         ly <= (int)(r >> 24);
 }
 
 struct RenderArgs {
@@ -135,9 +146,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 template <int NT, int CHUNK>
-__device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                            SRecs<CHUNK>& s_rec, uint32_t* s_idx, int64_t nbase, int ncount,
-                                            bool keep_copy = false) {
+__device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw, int th,
+                                            int64_t base, int count, SRecs<CHUNK>& s_rec, uint32_t* s_idx,
+                                            int64_t nbase, int ncount, bool keep_copy = false) {
   for (int j = threadIdx.x; j < count || j < ncount; j += NT) {
     uint32_t sn = 0xffffffffu;
     if (j < ncount) sn = __ldg(A.vals + nbase + j);
@@ -145,7 +156,8 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
       const uint32_t s = __ldg(A.vals + base + j);
       if (s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) {
         const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
-        unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j, keep_copy ? A.rcopy + (base + j) * REC_F4 : nullptr);
+        unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j, tx0, ty0, tw, th,
+                             keep_copy ? A.rcopy + (base + j) * REC_F4 : nullptr);
         if (s_idx) s_idx[j] = (uint32_t)rec;
       }
     }
@@ -163,12 +175,13 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
 // record index of each entry (for the gradient records) from the list, and
 // asks L2 for the contiguous records of the chunk processed next.
 template <int NT, int CHUNK>
-__device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                                SRecs<CHUNK>& s_rec, uint32_t* s_idx, int64_t nbase, int ncount) {
+__device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw,
+                                                int th, int64_t base, int count, SRecs<CHUNK>& s_rec,
+                                                uint32_t* s_idx, int64_t nbase, int ncount) {
   for (int j = threadIdx.x; j < count; j += NT) {
     const uint32_t s = __ldg(A.vals + base + j);
     if (!s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) continue;
-    unpack_record<CHUNK>(A.rcopy + (base + j) * REC_F4, s_rec, j);
+    unpack_record<CHUNK>(A.rcopy + (base + j) * REC_F4, s_rec, j, tx0, ty0, tw, th);
     s_idx[j] = (uint32_t)(vw.rbase + ((int64_t)s - vw.soff));
   }
   // 128-byte lines of the next chunk's records
@@ -183,13 +196,15 @@ __device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView
 // the warp ballots, per patch column and per patch row, which entries'
 // rects span it, and each lane ANDs its column's and its row's ballot.
 template <int CHUNK>
-__device__ __forceinline__ uint32_t lane_word(const SRecs<CHUNK>& s_rec, int wd, int count, int bx, int by, int lane) {
+__device__ __forceinline__ uint32_t lane_word(const SRecs<CHUNK>& s_rec, int wd, int count, int px0, int py0,
+                                              int lane) {
   const int j = wd * 32 + lane;
   uint32_t cm = 0, rm = 0;
   if (j < count) {
-    const int4 r = s_rec.rect[j];  // x0, y0, x1 - x0, y1 - y0
-    const int c0 = max(r.x - bx, 0), c1 = min(r.x + r.z - bx, 7);
-    const int r0 = max(r.y - by, 0), r1 = min(r.y + r.w - by, 3);
+    // (px0, py0): the patch's offset in the tile
+    const uint32_t r = __float_as_uint(s_rec.n[j].w);
+    const int c0 = max((int)(r & 0xffu) - px0, 0), c1 = min((int)((r >> 16) & 0xffu) - px0, 7);
+    const int r0 = max((int)((r >> 8) & 0xffu) - py0, 0), r1 = min((int)(r >> 24) - py0, 3);
     if (c0 <= c1 && r0 <= r1) {
       cm = ((2u << c1) - 1u) & ~((1u << c0) - 1u);
       rm = ((2u << r1) - 1u) & ~((1u << r0) - 1u);
@@ -334,14 +349,14 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         S.nact = 0;
         S.next = 0;
       }
-      stage_chunk<NT, CHUNK>(A, vw, base, count, S.rec, nullptr, base + CHUNK,
+      stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, base, count, S.rec, nullptr, base + CHUNK,
                              (int)max64(min64(CHUNK, (int64_t)range.y - base - CHUNK), 0), true);
       __syncthreads();
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
         if (__all_sync(0xffffffffu, done)) continue;
         const int nwd = (count + 31) >> 5;
-        for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx, by, lane);
+        for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
         int wd = 0;
         uint32_t b = done ? 0u : S.bits[wid][0][lane];
         for (;;) {
@@ -402,7 +417,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           int nrel = 0;
           for (int wd = 0; wd < (count + 31) >> 5; wd++) {
             const int j = wd * 32 + lane;
-            const bool rel = j < count && in_rect(S.rec.rect[j], qx, qy);
+            const bool rel = j < count && in_tile_rect(__float_as_uint(S.rec.n[j].w), qx - tx0, qy - ty0);
             const uint32_t bb = __ballot_sync(0xffffffffu, rel);
             if (rel) S.list[wid][nrel + __popc(bb & lt_mask)] = (uint16_t)j;
             nrel += __popc(bb);
@@ -691,7 +706,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
       const int64_t nlo = max64((int64_t)range.x, lo - CHUNK);  // the chunk in front, processed next
-      stage_chunk_seq<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
+      stage_chunk_seq<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
       __syncthreads();
       // per-pixel masks of this chunk, restricted to the entries below the pixel's last
       const int lim = act ? (int)min64((int64_t)my_last - lo, count) : 0;
@@ -701,7 +716,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         for (int wd = 0; wd < NWD; wd++) {
           uint32_t m = 0;
           if (wd < nwd) {
-            m = lane_word(S.rec, wd, count, bx, by, lane);
+            m = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
             const int keep = lim - wd * 32;
             m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
             S.pbits[myslot][wd] = m;
@@ -975,13 +990,13 @@ __global__ void __launch_bounds__(TW* TH) k_max_error(const RenderArgs A, const 
     for (int64_t lo = range.x; lo < (int64_t)top; lo += CHUNK) {
       const int count = (int)min64(CHUNK, (int64_t)top - lo);
       const int nwd = (count + 31) >> 5;
-      stage_chunk<NT, CHUNK>(A, vw, lo, count, S.rec, nullptr, lo + CHUNK,
+      stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, nullptr, lo + CHUNK,
                              (int)max64(min64(CHUNK, (int64_t)top - lo - CHUNK), 0));
       for (int j = threadIdx.x; j < count; j += NT) S.emax[j] = 0u;
       __syncthreads();
       const int lim = (int)min64(max64((int64_t)my_last - lo, 0), count);
       for (int wd = 0; wd < nwd; wd++) {
-        uint32_t b = lane_word(S.rec, wd, count, bx, by, lane);
+        uint32_t b = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
         const int keep = lim - wd * 32;
         b = keep >= 32 ? b : (keep <= 0 ? 0u : (b & ((1u << keep) - 1u)));
         while (b) {
