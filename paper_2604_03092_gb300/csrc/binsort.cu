@@ -346,7 +346,8 @@ struct RegSortSmem {
 
 template <int NWARPS, int ITEMS>
 __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned long long* b, int n, uint16_t* cnt,
-                                               uint32_t* tot, uint32_t dmin, uint32_t imin, int ishift, int nbits) {
+                                               uint32_t* tot, uint32_t dmin, uint32_t imin, int ishift, int nbits,
+                                               int lsb = 0) {
   constexpr int NT = NWARPS * 32, CP = RegSortSmem<NWARPS>::CP;
   static_assert(NWARPS % 8 == 0, "the counter scan takes 8 counters per thread");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -377,7 +378,7 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
           const unsigned long long dk = (unsigned long long)((uint32_t)(key[k] >> 32) - dmin);
           const unsigned long long kk =
               ishift < 0 ? dk : ((dk << ishift) | (unsigned long long)((uint32_t)key[k] - imin));
-          d = (uint32_t)(kk >> shift) & 0xffu;
+          d = (uint32_t)(kk >> (shift + lsb)) & 0xffu;
         }
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
@@ -450,10 +451,12 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
 
 // Sort a bucket of at most NWARPS * 32 * ITEMS composites by (depth bits,
 // surfel index): load it from global memory into shared memory (finding the
-// bucket's depth and index ranges on the way), sort the depth bits relative
-// to the smallest depth, put equal depths in surfel order in place (a run of
-// more than 64 equal depths triggers one exact re-sort on the relative
-// composite key instead).  Returns the shared buffer holding the result.
+// bucket's depth and index ranges on the way), radix-sort the top 16 bits of
+// the depth relative to the smallest depth (two passes where the depths span
+// more), then put each run of entries that tie on those bits in (depth,
+// surfel) order in place by insertion (a run longer than 64 triggers one
+// exact re-sort on the relative composite key instead).  Returns the shared
+// buffer holding the result.
 template <int NWARPS, int ITEMS>
 __device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restrict__ g, int n,
                                                unsigned long long* sa, unsigned long long* sb, uint16_t* cnt,
@@ -480,14 +483,18 @@ __device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restr
   __syncthreads();
   const uint32_t dmin = red[0], dbits = (uint32_t)bits_of(red[1] - red[0]);
   const uint32_t imin = red[2], ibits = (uint32_t)bits_of(red[3] - red[2]);
-  unsigned long long* r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits);
+  // radix passes over the top 16 bits of the relative depth only; entries
+  // that tie there form runs, put in (depth, surfel) order in place below
+  const int lsb = max((int)dbits - 16, 0);
+  unsigned long long* r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits - lsb, lsb);
+  auto top = [&](int i) -> uint32_t { return ((uint32_t)(r[i] >> 32) - dmin) >> lsb; };
   for (int i = threadIdx.x; i < n; i += NT) {
-    const uint32_t d = (uint32_t)(r[i] >> 32);
-    const bool starts = (i == 0 || (uint32_t)(r[i - 1] >> 32) != d) && i + 1 < n && (uint32_t)(r[i + 1] >> 32) == d;
+    const uint32_t d = top(i);
+    const bool starts = (i == 0 || top(i - 1) != d) && i + 1 < n && top(i + 1) == d;
     if (!starts) continue;
     int e = i + 1;
-    while (e + 1 < n && e - i < 64 && (uint32_t)(r[e + 1] >> 32) == d) e++;
-    if (e + 1 < n && (uint32_t)(r[e + 1] >> 32) == d) {
+    while (e + 1 < n && e - i < 64 && top(e + 1) == d) e++;
+    if (e + 1 < n && top(e + 1) == d) {
       red[4] = 1u;
       continue;
     }
