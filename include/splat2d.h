@@ -212,8 +212,9 @@ int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, voi
  * tile stages chunks of its sorted surfels in shared memory and composites
  * front to back with warp-level early termination.  Writes rgb, depth,
  * normal, alpha (packed per view as described above; any may be NULL) and
- * keeps per-pixel T_final and the last blended index in `ws` for the
- * backward pass.
+ * keeps in `ws`, for the backward pass, per-pixel T_final and the last
+ * blended index and a copy of every record it staged, in sorted-list order
+ * (the workspace holds instance_capacity such 80-byte records).
  */
 int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
                        float* rgb, float* depth, float* normal, float* alpha, splat2d_stream stream);
@@ -222,11 +223,14 @@ int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, v
  * Reverse pass: walks each pixel back to front from its last blended surfel,
  * recovering the transmittance by division instead of storing per-pixel
  * lists (32 (pixel, surfel) pairs per warp step, with segmented warp scans);
- * per-surfel gradients are summed across the tile in shared memory before
- * one vector atomic per (tile, surfel); then a per-surfel pass chains them to
- * the parameters and reduces the per-view pose tangent.  d_* are upstream gradients laid out like the
- * forward outputs (NULL = zero).  Must follow splat2d_render_fwd on the same
- * workspace with unchanged surfels.
+ * it reads the records from the sorted-order copy the forward left.
+ * Per-surfel gradients are summed across the tile in shared memory (in
+ * fixed point, each term rounded to a power-of-two fraction of the tile's
+ * typical sum; terms outside that range are added exactly in global memory)
+ * before one vector atomic per (tile, surfel); then a per-surfel pass chains
+ * them to the parameters and reduces the per-view pose tangent.  d_* are
+ * upstream gradients laid out like the forward outputs (NULL = zero).  Must
+ * follow splat2d_render_fwd on the same workspace with unchanged surfels.
  */
 int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
                        void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth,
