@@ -42,3 +42,14 @@ def test_lookup_reads_three_field_entries_and_shipped_table(tmp_path, monkeypatc
     monkeypatch.setitem(autotune.SHIPPED, key, (8, 8, 128, 64))
     assert autotune.lookup(sc.views, sc.n, path=empty) == (8, 8, 128, 64)
     assert autotune.lookup(sc.views, sc.n, path=empty, shipped=False) is None
+
+
+def test_shipped_shapes_are_candidates_the_library_accepts():
+    # tile shapes and chunk depths the C library's config check takes
+    tiles = {(16, 16), (8, 8), (32, 8)}
+    for key, c in autotune.SHIPPED.items():
+        assert c in autotune.CANDIDATES, (key, c)
+        tw, th, ch, bch = c
+        assert (tw, th) in tiles
+        for depth in (ch, bch):
+            assert depth in (64, 128, 256) or (depth == 512 and tw * th == 256)
