@@ -34,19 +34,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "2DGS raster fwd+bwd ms/view & views/s at 6.3M surfels; fraction of roofline"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128   # FP32 lanes per SM (4 sub-partitions x 32)
+MUFU_LANES_PER_SM = 16    # special-function (ex2, rcp) results per SM per clock
 
-# FP32 work per (pixel, surfel) pair of the compositing kernels, counted from
-# the arithmetic of the method (an FMA counts 2):
-#   alpha of a pair: pixel offset from the float-float center 4, the three
-#   ray-splat numerators/denominator 10, rho_obj 5, rho_lowpass 5, select 1,
-#   exponent argument 1, sigma*G 1, clamp and threshold 2            -> 29
-#   blend of a kept pair: T' 2, w 1, 7 accumulations (rgb, depth, normal) 14,
-#   stop test 1                                                       -> 18
-#   reverse of a kept pair: T recovery 2, w 1, upstream dot 13, d alpha 4,
-#   suffix update 2, 7 colour/depth/normal grads 7, opacity 1, d rho 3,
-#   geometry grads 20, center grads 10                                -> 63
+# Algorithmic work per unit of each stage, as the method defines it (the
+# counts the kernels report times these figures; nothing here is measured):
+#   compositing forward, per processed (pixel, surfel) pair -- every entry up
+#   to the pixel's stop whose rect holds the pixel, skipped or blended: about
+#   32 FP32 lane-instructions and 2 special-function ops (rcp, ex2); per
+#   instance the 4-byte list entry and the 76-byte record read once; per
+#   pixel 40 bytes of outputs and per-pixel state written.
+#   compositing backward, per processed pair: about 100 FP32
+#   lane-instructions and 3 special-function ops; per instance the 80-byte
+#   record read once; per pixel 72 bytes of upstream gradient and state
+#   read; per visible (view, surfel) its 80-byte gradient record written.
+INSTR_FWD, MUFU_FWD = 32, 2
+INSTR_BWD, MUFU_BWD = 100, 3
+FWD_BYTES_INST, FWD_BYTES_PIX = 80, 40
+BWD_BYTES_INST, BWD_BYTES_PIX, BWD_BYTES_VIS = 80, 72, 80
+
+# The same kernels' own FP32 arithmetic per pair, counted from their source
+# (an FMA counts 2), reported beside the figures above:
+#   alpha of a pair 29 FLOP; blend of a kept pair 18; reverse of a kept pair 63.
 FLOP_EVAL = 29
 FLOP_BLEND = 18
 FLOP_BWD = 63
@@ -166,27 +175,40 @@ def _omp_threads() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
+def _config(args, wl_desc, sc, world):
+    """The workload's description, identical in both arms' lines."""
+    return {"workload": args.workload, "description": wl_desc, "views": len(sc.views), "surfels": sc.n,
+            "l2": "inputs larger than L2 (records + instances > 129 MB)",
+            "parallelism": f"{world} independent submap(s), one per GPU"}
+
+
 def run_reference(args, wl_desc, make):
+    """The oracle on the host cores.  One step renders one whole view of the
+    workload (its preprocess, the forward and reverse pass at every pixel and
+    the chain rule; views in turn), so ms_per_step is the measured time of
+    one such step and value the views per second it sustains."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     sc = make(0)
-    times = []
+    times, descs = [], []
     for i in range(args.warmup + args.steps):
-        # one step: one whole view of the workload (views in turn)
         per_view, desc, wall = oracle_views(sc, [i % len(sc.views)], seed=i)
         if i >= args.warmup:
             times.append(per_view)
-    per_view = float(np.mean(times))
-    value = 1.0 / per_view
+            descs.append(i % len(sc.views))
+    per_step = float(np.mean(times))
+    value = 1.0 / per_step
+    sample = (f"one whole view of the {len(sc.views)}-view workload per step (views {descs} in turn): oracle "
+              f"preprocess of the view's surfels, forward and reverse pass at every pixel, chain rule; "
+              f"{_omp_threads()} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_view * len(sc.views) * 1e3,
-        "ms_per_view": per_view * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": wl_desc, "views": len(sc.views), "surfels": sc.n},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "views_per_step": 1,
+        "ms_per_view": per_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": _config(args, wl_desc, sc, args.gpus),
         "cpu_baseline": {"value": value, "unit": "views/s", "cores": _omp_threads(), "kind": "oracle",
-                         "sample": desc},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -199,13 +221,16 @@ STAGE_SOURCE = {"render_bwd": "render.cu", "render_fwd": "render.cu", "preproces
                 "preprocess_bwd": "preprocess.cu", "bin_sort": "binsort.cu"}
 
 
-def _recorded_traffic(workload: str, stage: str, cfg):
-    """DRAM bytes per launch of the stage's kernel from the ncu capture
-    recorded in profiles/traffic_<workload>.txt, if it was taken on the
-    current kernel source (sha256 of its .cu file) and launch shape; else
-    None."""
+def _recorded_traffic(stage: str, cfg, n_inst: int):
+    """DRAM bytes per launch of the stage's kernel at this launch's
+    instance count, scaled from the ncu capture recorded on the smaller
+    8-keyframe submap (profiles/traffic_<kernel>_submap8.txt: captures that
+    hold a few GB on the device) by the ratio of instances, which is what the
+    compositing kernels' traffic grows with; None unless the capture was
+    taken on the current kernel source (sha256 of its .cu file) and launch
+    shape."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
+    path = os.path.join(ROOT, "profiles", f"traffic_k_{stage}_submap8.txt")
     if not os.path.exists(path):
         return None
     rec = {}
@@ -223,8 +248,8 @@ def _recorded_traffic(workload: str, stage: str, cfg):
     if rec.get("launch_shape") != shape:
         return None
     try:
-        return int(rec["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
+        return int(int(rec["dram_bytes_per_launch"]) * n_inst / int(rec["instances"]))
+    except (KeyError, ValueError, ZeroDivisionError):
         return None
 
 
@@ -517,46 +542,61 @@ def main():
     lay = rast.layout
     n_vis = st["n_visible"]
     n_inst = st["n_instances"]
-    passes = (32 + max(int(lay.n_tiles - 1).bit_length(), 0) + 7) // 8
-    work = {
-        # parameters read once per surfel (all views of a workload form one group), a tile count per
-        # (view, surfel) record, an 80-byte render record per visible pair
-        "preprocess": ("hbm", 56 * rast.n_surfels + 4 * lay.n_records + 80 * n_vis),
-        "bin_sort": ("hbm", 8 * lay.n_records + 32 * n_vis + 8 * n_inst + 20 * n_inst),
-        "render_fwd": ("alu", FLOP_EVAL * st["fwd_pairs_evaluated"] + FLOP_BLEND * st["fwd_pairs_blended"]),
-        "render_bwd": ("alu", FLOP_EVAL * st["bwd_pairs_evaluated"] + FLOP_BWD * st["bwd_pairs_blended"]),
-        "preprocess_bwd": ("hbm", 4 * lay.n_records + 80 * n_vis + 56 * rast.n_surfels + 52 * rast.n_surfels),
+    # Each stage's ideal time is the largest of its algorithmic bytes over
+    # the measured copy bandwidth, its FP32 lane-instructions over the FP32
+    # lane rate and its special-function ops over the MUFU rate, with the
+    # SM count read from the device and the maximum SM clock; the stage's
+    # fraction is ideal / measured, and the binding term names its bound.
+    n_sm = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    clk_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    instr_peak = n_sm * FP32_LANES_PER_SM * clk_hz      # lane-instructions / s
+    mufu_peak = n_sm * MUFU_LANES_PER_SM * clk_hz
+    bw = peaks["hbm_gbs"] * 1e9
+    n_pix = rast.n_pixels
+    pe_f, pe_b = st["fwd_pairs_evaluated"], st["bwd_pairs_evaluated"]
+    work = {  # stage: (bytes, FP32 lane-instructions, MUFU ops)
+        "preprocess": (56 * rast.n_surfels + 4 * lay.n_records + 80 * n_vis, 0, 0),
+        "bin_sort": (8 * lay.n_records + 32 * n_vis + 8 * n_inst + 20 * n_inst, 0, 0),
+        "render_fwd": (FWD_BYTES_INST * n_inst + FWD_BYTES_PIX * n_pix, INSTR_FWD * pe_f, MUFU_FWD * pe_f),
+        "render_bwd": (BWD_BYTES_INST * n_inst + BWD_BYTES_PIX * n_pix + BWD_BYTES_VIS * n_vis,
+                       INSTR_BWD * pe_b, MUFU_BWD * pe_b),
+        "preprocess_bwd": (4 * lay.n_records + 80 * n_vis + 56 * rast.n_surfels + 52 * rast.n_surfels, 0, 0),
     }
-    dom = max(stage_ms, key=lambda s: stage_ms[s])
-    bound, amount = work[dom]
-    sec = stage_ms[dom] / 1e3
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
     stage_frac = {}
-    for s in stages:
-        b_, a_ = work[s]
-        t_ = stage_ms[s] / 1e3
-        if b_ == "hbm":
-            stage_frac[s] = {"bound": "hbm", "achieved_gbs": a_ / t_ / 1e9, "frac": a_ / t_ / 1e9 / peaks["hbm_gbs"],
-                             "ms": stage_ms[s]}
-        else:
-            stage_frac[s] = {"bound": "alu", "achieved_tflops": a_ / t_ / 1e12, "frac": a_ / t_ / 1e12 / alu_peak,
-                             "ms": stage_ms[s]}
-    # composite fraction: the time the stages would take at their bounds
-    # (algorithmic work / peak) over the time they took
-    t_ideal = sum((work[s_][1] / (peaks["hbm_gbs"] * 1e9)) if work[s_][0] == "hbm"
-                  else (work[s_][1] / (alu_peak * 1e12)) for s_ in stages)
-    composite = t_ideal / (sum(stage_ms.values()) / 1e3)
-    traffic = _recorded_traffic(args.workload, dom, cfg)
-    if bound == "hbm":
-        achieved = amount / sec / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+    t_ideal_sum = 0.0
+    for s_ in stages:
+        b_, i_, m_ = work[s_]
+        t_ = stage_ms[s_] / 1e3
+        terms = {"hbm": b_ / bw, "alu": i_ / instr_peak, "mufu": m_ / mufu_peak}
+        bound = max(terms, key=terms.get)
+        t_ideal_sum += terms[bound]
+        stage_frac[s_] = {"bound": bound, "frac": terms[bound] / t_, "ms": stage_ms[s_],
+                          "ideal_ms": terms[bound] * 1e3, "bytes": b_, "lane_instr": i_, "mufu": m_,
+                          "achieved_gbs": b_ / t_ / 1e9, "frac_hbm": terms["hbm"] / t_,
+                          "frac_alu": terms["alu"] / t_}
+    stage_frac["render_fwd"]["flop"] = FLOP_EVAL * pe_f + FLOP_BLEND * st["fwd_pairs_blended"]
+    stage_frac["render_bwd"]["flop"] = FLOP_EVAL * pe_b + FLOP_BWD * st["bwd_pairs_blended"]
+    composite = t_ideal_sum / (sum(stage_ms.values()) / 1e3)
+    dom = max(stage_ms, key=lambda s: stage_ms[s])
+    sec = stage_ms[dom] / 1e3
+    d = stage_frac[dom]
+    traffic = _recorded_traffic(dom, cfg, n_inst)
+    if d["bound"] == "hbm":
+        roof = {"bound": "hbm", "kernel": dom, "achieved": d["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": d["frac"], "traffic": traffic,
                 "peak_source": f"{peaks['source']} STREAM-style copy"}
     else:
-        achieved = amount / sec / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (FP32 FMA pipe)"}
+        unit_peak = instr_peak if d["bound"] == "alu" else mufu_peak
+        amount = d["lane_instr"] if d["bound"] == "alu" else d["mufu"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": amount / sec / 1e12, "peak": unit_peak / 1e12,
+                "unit": "Tinstr/s", "frac": d["frac"], "traffic": traffic,
+                "peak_source": (f"{n_sm} SMs (device) x {FP32_LANES_PER_SM if d['bound'] == 'alu' else MUFU_LANES_PER_SM}"
+                                f" lanes x {clk_hz / 1e6:.0f} MHz")}
+    roof["work"] = {"bytes": d["bytes"], "lane_instr": d["lane_instr"], "mufu": d["mufu"],
+                    "frac_hbm": d["frac_hbm"], "frac_alu": d["frac_alu"], "sm_count": n_sm,
+                    "per_unit": ({"instr_per_pair": INSTR_BWD, "mufu_per_pair": MUFU_BWD,
+                                  "bytes_per_instance": BWD_BYTES_INST, "bytes_per_pixel": BWD_BYTES_PIX,
+                                  "bytes_per_visible": BWD_BYTES_VIS} if dom == "render_bwd" else None)}
 
     # ---- CPU baseline (the oracle, host cores, bounded sample) -----------------
     cpu = None
@@ -571,11 +611,10 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "ms_per_view": ms_per_step / V,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ray-cast indoor submap; stands in for ScanNet/BundleFusion)",
-            "config": {"workload": args.workload, "description": wl_desc, "views": V, "surfels": sc.n,
-                       "tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk,
+            "views_per_step": V, "config": _config(args, wl_desc, sc, world),
+            "launch": {"tile": f"{cfg.tile_w}x{cfg.tile_h}", "chunk": cfg.chunk,
                        "bwd_chunk": cfg.bwd_chunk or cfg.chunk, "fwd_tail": cfg.fwd_tail, "instances": n_inst,
-                       "visible_pairs": n_vis, "l2": "inputs larger than L2 (records + instances > 129 MB)",
-                       "parallelism": f"{world} independent submap(s), one per GPU"},
+                       "visible_pairs": n_vis},
             "stages_ms": stage_ms, "stage_roofline": stage_frac, "composite_roofline_frac": composite,
             "roofline": roof, "clocks": clocks,
             "graph_views_per_s": graph_vps, "plain_per_view_views_per_s": plain_vps,

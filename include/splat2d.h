@@ -178,6 +178,11 @@ void splat2d_default_config(splat2d_config* cfg);
 size_t splat2d_workspace_size(const splat2d_config* cfg, const splat2d_problem* prob);
 
 /*
+ * Follows: Sec. 3 ("Preliminaries"), the 2DGS surfel the paper adopts
+ * (position, colour, opacity, rotation, 2D scale) and the per-surfel terms
+ * of Eq. 1 (the weight w_i of a pixel, the depth z_i along the optical
+ * axis); the extent is the support of w_i >= alpha_min.
+ *
  * Per-surfel preprocess (one launch over every view's surfel range): camera
  * transform, tangent frame from the normalised quaternion, the ray-splat
  * intersection transform, projected center, depth key, camera normal turned
@@ -191,6 +196,10 @@ int splat2d_preprocess(const splat2d_config* cfg, const splat2d_problem* prob, c
                        void* ws, size_t ws_bytes, splat2d_stream stream);
 
 /*
+ * Follows: Eq. 1 (Sec. 3) blends surfels front to back in depth order, and
+ * the paper renders the map "through standard rasterization" (Sec. 4.1,
+ * the rendering loss): tile binning and a depth sort per tile.
+ *
  * Tile binning and sort: every visible (view, surfel) pair emits one
  * instance per tile of its rect, key = (global tile) << 32 | FP32 depth bits,
  * value = surfel index, and the instances are put in key order, ties in
@@ -208,6 +217,9 @@ int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, voi
                      splat2d_stream stream);
 
 /*
+ * Follows: Eq. 1 (Sec. 3), the alpha blending of colour, depth and
+ * accumulation, I, D, A = sum_i (c_i, z_i, 1) w_i prod_{j<i} (1 - w_j).
+ *
  * Forward compositing: one persistent launch over every (view, tile); each
  * tile stages chunks of its sorted surfels in shared memory and composites
  * front to back with warp-level early termination.  Writes rgb, depth,
@@ -220,6 +232,11 @@ int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, v
                        float* rgb, float* depth, float* normal, float* alpha, splat2d_stream stream);
 
 /*
+ * Follows: the analytic gradient of Eq. 1 (Sec. 3) with respect to the
+ * surfel parameters and the camera pose, which the backend's rendering-based
+ * refinement of the map over the latest keyframes needs (Sec. 4.3,
+ * "Lightweight Map Refinement").
+ *
  * Reverse pass: walks each pixel back to front from its last blended surfel,
  * recovering the transmittance by division instead of storing per-pixel
  * lists (32 (pixel, surfel) pairs per warp step, with segmented warp scans);

@@ -68,6 +68,8 @@ def _load():
         lib.oracle_render_pixels.argtypes = [ctypes.c_int, i64] + [P] * 8 + [i64, P] + [P] * 4
         lib.oracle_render_bwd.argtypes = [ctypes.c_int, i64] + [P] * 9 + [i64, P, P]
         lib.oracle_chain.argtypes = [i64] + [P] * 12
+        lib.oracle_render_pixels_variants.argtypes = ([ctypes.c_int, i64] + [P] * 8
+                                                      + [ctypes.c_int, ctypes.c_int, i64, P, P])
         lib.oracle_max_error.argtypes = [ctypes.c_int, i64] + [P] * 8 + [P, P]
         lib.oracle_bin_sort.argtypes = [ctypes.c_int] + [P] * 9 + [i64]
         lib.oracle_bin_sort.restype = i64
@@ -99,13 +101,16 @@ class Config:
     # depth output: False = the surfel center's depth (Eq. 1), True = the depth
     # of the ray-splat intersection where the object-space term decides
     depth_ray: bool = False
+    # binned mode: which pixel rect decides whether a pair counts (0 = the
+    # extent's; 1 / 2 = the widest / narrowest that rounding could give)
+    rect_variant: int = 0
 
     def array(self) -> np.ndarray:
         f32 = lambda x: float(np.float32(x))  # the library receives FP32 constants
         return np.array([f32(self.alpha_min), f32(self.alpha_max), f32(self.t_min), f32(self.sigma_lp),
                          f32(self.z_near), f32(self.bg[0]), f32(self.bg[1]), f32(self.bg[2]),
                          self.tile_w, self.tile_h, self.eps_alpha, self.eps_t, self.eps_px, self.eps_z,
-                         1.0 if self.depth_ray else 0.0],
+                         1.0 if self.depth_ray else 0.0, float(self.rect_variant)],
                         dtype=np.float64)
 
 
@@ -281,3 +286,35 @@ def bin_sort(preps, tile_bases, tiles_x, surfel_offsets, cap: Optional[int] = No
     lib.oracle_bin_sort(len(preps), _p(counts), _p(status), _p(tr), _p(zb), _p(sidx), _p(tb), _p(tx),
                         _p(keys), _p(vals), need)
     return keys[:need], vals[:need]
+
+
+def render_pixels_either_side(prep: Prep, pix: np.ndarray, mode: int = 1) -> np.ndarray:
+    """Outputs (k, 8, npix) at the listed pixels under every combination of
+    the outcomes of the decisions this oracle reports as within rounding:
+    alpha_min and t_min moved just past their flag margins either way (so a
+    pair whose alpha, or a stop whose transmittance, is within the margin is
+    decided the other way), and the pixel rect of the extent, the widest or
+    the narrowest that rounding could give.  A result computed at lower
+    precision that took some of these decisions the other way should match
+    one of the k outputs; k = 27 (the unmodified result is among them)."""
+    lib = _load()
+    base = np.asarray(prep.cfg, np.float64)
+    ea, et = base[10], base[11]
+    rows = []
+    for sa in (0, -1, 1):
+        for st in (0, -1, 1):
+            for rv in (0, 1, 2):
+                c = base.copy()
+                c[0] = base[0] * (1.0 + 1.25 * sa * ea)
+                c[2] = base[2] * (1.0 + 1.25 * st * et)
+                c[15] = rv
+                rows.append(c)
+    cfgs = np.ascontiguousarray(np.stack(rows))
+    pix = _c(pix, np.int64)
+    out = np.zeros((len(rows), 8, pix.shape[0]))
+    if pix.shape[0]:
+        lib.oracle_render_pixels_variants(mode, prep.rec.shape[0], _p(prep.rec), _p(prep.status),
+                                          _p(prep.pixrect), _p(prep.amb), _p(prep.zbits), _p(prep.sflags),
+                                          _p(prep.cam), _p(cfgs), cfgs.shape[0], cfgs.shape[1], pix.shape[0],
+                                          _p(pix), _p(out))
+    return out

@@ -78,6 +78,13 @@ typedef struct {
   int tile_w, tile_h;
   double eps_alpha, eps_t, eps_px, eps_z;
   int depth_ray;  /* depth output: 0 = z_i of the center, 1 = depth of the ray-splat intersection */
+  /* Which pixel rect decides whether a pair counts in binned mode: 0 = the
+   * rect of the extent (the definition), 1 = the widest and 2 = the
+   * narrowest rect that rounding of the extent could give.  Variants 1 and 2
+   * state the two outcomes of a rect edge within rounding of a pixel center,
+   * so that a result taken at lower precision can be checked against either
+   * side of that decision instead of being dropped. */
+  int rect_variant;
 } cfg_t;
 
 /* cam: W, H, fx, fy, cx, cy, then the 3x4 world-to-camera matrix row-major. */
@@ -96,7 +103,7 @@ static void load_cam(const double* c, cam_t* k) {
 }
 
 /* cfg: alpha_min, alpha_max, t_min, sigma_lp, z_near, bg[3], tile_w, tile_h,
- * eps_alpha, eps_t, eps_px, eps_z, depth_ray. */
+ * eps_alpha, eps_t, eps_px, eps_z, depth_ray, rect_variant. */
 static void load_cfg(const double* c, cfg_t* k) {
   k->alpha_min = c[0]; k->alpha_max = c[1]; k->t_min = c[2];
   k->sigma_lp = c[3]; k->z_near = c[4];
@@ -104,6 +111,7 @@ static void load_cfg(const double* c, cfg_t* k) {
   k->tile_w = (int)c[8]; k->tile_h = (int)c[9];
   k->eps_alpha = c[10]; k->eps_t = c[11]; k->eps_px = c[12]; k->eps_z = c[13];
   k->depth_ray = c[14] != 0.0;
+  k->rect_variant = (int)c[15];
 }
 
 /* Rotation matrix of a unit quaternion (w, x, y, z), row-major. */
@@ -497,6 +505,10 @@ static int64_t walk_pixel(const view_t* V, const cfg_t* cfg, int ix, int iy, dou
     if (V->mode == 1) {
       if (!in_rect(V->amb + 8 * s, ix, iy)) continue;
       counts = (st == ST_VISIBLE) && in_rect(V->pixrect + 4 * s, ix, iy);
+      if (cfg->rect_variant == 1)  /* widest: the loop above already required it */
+        counts = st == ST_VISIBLE || st == ST_EMPTY;
+      else if (cfg->rect_variant == 2)  /* narrowest */
+        counts = (st == ST_VISIBLE) && in_rect(V->amb + 8 * s + 4, ix, iy);
       if (!in_rect(V->amb + 8 * s + 4, ix, iy)) maybe |= PF_RECT;
     } else {
       counts = (st == ST_VISIBLE || st == ST_EMPTY);
@@ -600,6 +612,36 @@ int oracle_render_pixels(int mode, int64_t n, const double* rec, const int32_t* 
     nblend[i] = (int32_t)nb;
     pflags[i] = fl;
   }
+  free_view(&V);
+  return 0;
+}
+
+/*
+ * The listed pixels under k configurations (cfgv: k rows of cfg values that
+ * differ only in their thresholds and rect_variant; the first row's tile
+ * size builds the view); out is [k][8][npix].  Used to check a pixel whose
+ * decisions are within rounding against each outcome of those decisions.
+ */
+int oracle_render_pixels_variants(int mode, int64_t n, const double* rec, const int32_t* status,
+                                  const int32_t* pixrect, const int32_t* amb, const uint32_t* zbits,
+                                  const uint32_t* sflags, const double* camv, const double* cfgv, int k,
+                                  int ncfg, int64_t npix, const int64_t* pix, double* out) {
+  cam_t cam;
+  cfg_t cfg0;
+  load_cam(camv, &cam);
+  load_cfg(cfgv, &cfg0);
+  view_t V;
+  build_view(&V, mode, n, rec, status, pixrect, amb, zbits, sflags, &cam, &cfg0);
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+  for (int c = 0; c < k; c++)
+    for (int64_t i = 0; i < npix; i++) {
+      cfg_t cfg;
+      load_cfg(cfgv + (int64_t)c * ncfg, &cfg);
+      int ix = (int)(pix[i] % cam.W), iy = (int)(pix[i] / cam.W);
+      double o8[8];
+      walk_pixel(&V, &cfg, ix, iy, o8, NULL, NULL, NULL, NULL, 0);
+      for (int ch = 0; ch < 8; ch++) out[((int64_t)c * 8 + ch) * npix + i] = o8[ch];
+    }
   free_view(&V);
   return 0;
 }

@@ -125,6 +125,9 @@ class Rasterizer:
         self.uniform = len(set(self.sizes)) == 1
         self.n_records = sum(int(self._cviews[i].surfel_count) for i in range(self.n_views))
         self._cfg = self.config.to_c()
+        # bumped by every preprocess: the workspace then holds another
+        # forward's records, lists and per-pixel state
+        self.generation = 0
         cap = capacity if capacity is not None else max(1 << 16, int(1.5 * self.n_records))
         self._alloc(cap)
 
@@ -202,9 +205,20 @@ class Rasterizer:
         return s
 
     # -- calls -------------------------------------------------------------
+    def set_view_pose(self, v: int, Rt):
+        """Replace view v's world-to-camera pose (3x4, row-major); takes
+        effect from the next preprocess.  A pose step along the tangent the
+        backward returns is T_cw <- Exp(xi) T_cw, folded in by the caller."""
+        vals = [float(x) for x in (Rt.reshape(-1).tolist() if hasattr(Rt, "reshape") else Rt)]
+        if len(vals) != 12:
+            raise ValueError("Rt: 12 values (3x4 row-major)")
+        for k in range(12):
+            self._cviews[v].Rt[k] = vals[k]
+
     def preprocess(self, means, scales, quats, opacity, rgb):
         if means.shape[0] != self.n_surfels:
             raise ValueError(f"expected {self.n_surfels} surfels, got {means.shape[0]}")
+        self.generation += 1
         self._sf = self._surfels(means, scales, quats, opacity, rgb)
         _abi.check(self.lib.splat2d_preprocess(ctypes.byref(self._cfg), ctypes.byref(self._prob),
                                                ctypes.byref(self._sf), self._ws_ptr, self.ws_bytes, _stream()),
@@ -331,14 +345,26 @@ def accum_gate(alpha: torch.Tensor, tau: float):
 
 class Splat2DRender(torch.autograd.Function):
     """Differentiable render of all views of `rast`: returns (rgb, depth,
-    normal, alpha).  `pose_tangent` ([V, 6]) receives dL/dxi of each view's
-    pose under T_cw <- Exp(xi) T_cw at xi = 0; its value is not used."""
+    normal, alpha).
+
+    `pose_tangent` ([V, 6]) receives dL/dxi of each view's pose under the
+    left perturbation T_cw <- Exp(xi) T_cw, evaluated at xi = 0.  Its value
+    does not enter the render: the poses are the rasterizer's views, so a
+    caller that refines poses folds each step into them
+    (`Rasterizer.set_view_pose`) and keeps xi at zero.
+
+    The intermediate state the backward needs (records, sorted lists,
+    per-pixel transmittance) lives in `rast`'s one workspace, so a second
+    render with the same rasterizer overwrites it: the first render's
+    backward then raises instead of returning gradients of the wrong forward.
+    Use one Rasterizer per render that must stay differentiable."""
 
     @staticmethod
     def forward(ctx, rast: Rasterizer, means, scales, quats, opacity, rgb, pose_tangent, check: bool = True):
         params = [t.contiguous() for t in (means, scales, quats, opacity, rgb)]
         out = rast.forward(*params, check=check)
         ctx.rast = rast
+        ctx.generation = rast.generation
         ctx.save_for_backward(*params)
         shaped = rast.shaped(out)
         return tuple(shaped)
@@ -346,6 +372,10 @@ class Splat2DRender(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g_rgb, g_depth, g_normal, g_alpha):
         rast: Rasterizer = ctx.rast
+        if rast.generation != ctx.generation:
+            raise RuntimeError("Splat2DRender: the rasterizer ran another forward after this one, so its "
+                               "workspace no longer holds this render's state; use one Rasterizer per "
+                               "render that is differentiated")
         params = ctx.saved_tensors
         grads = rast.backward(*params, (g_rgb, g_depth, g_normal, g_alpha))
         return (None, grads.means, grads.scales, grads.quats, grads.opacity, grads.rgb, grads.pose, None)

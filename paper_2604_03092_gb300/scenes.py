@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 from typing import List, Optional
 
 import numpy as np
@@ -307,12 +308,25 @@ def _render_keyframe(L: _Layout, Rt: np.ndarray, W: int, H: int, f: float):
     return depth.reshape(H, W), X.reshape(H, W, 3), col.reshape(H, W, 3), dc
 
 
+def _render_keyframes(L: _Layout, poses, W: int, H: int, f: float):
+    """_render_keyframe of every pose, in order; the ray casts run on a
+    thread pool (they draw no random numbers, so the results are those of a
+    sequential loop)."""
+    import concurrent.futures
+    workers = max(1, min(len(poses), os.cpu_count() or 1, 16))
+    if workers == 1:
+        return [_render_keyframe(L, P, W, H, f) for P in poses]
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(lambda P: _render_keyframe(L, P, W, H, f), poses))
+
+
 def _surfels_from_keyframe(L: _Layout, Rt: np.ndarray, W: int, H: int, f: float,
-                           rng: np.random.Generator):
+                           rng: np.random.Generator, rendered=None):
     """One surfel per pixel: unprojected center, normal from depth gradients,
     tangent u = camera x projected on the plane, scales = pixel footprint x
-    U[0.8, 1.5] per axis, procedural colour, opacity U[0.5, 1]."""
-    depth, Xw, col, dc = _render_keyframe(L, Rt, W, H, f)
+    U[0.8, 1.5] per axis, procedural colour, opacity U[0.5, 1].  `rendered`
+    is this pose's _render_keyframe result, if already computed."""
+    depth, Xw, col, dc = rendered if rendered is not None else _render_keyframe(L, Rt, W, H, f)
     Pc = dc.reshape(H, W, 3) * depth[..., None]
     gx = np.gradient(Pc, axis=1)
     gy = np.gradient(Pc, axis=0)
@@ -417,7 +431,11 @@ def submap_scene(seed: int = 2001, n_keyframes: int = 32, width: int = 512, heig
     rng = np.random.default_rng(seed)
     L = _layout(n_rooms, rng, boxes_per_room=10, gains=gains)
     poses = _trajectory(L, rng, n_keyframes, step, deg)
-    parts = [_surfels_from_keyframe(L, P, width, height, f, rng) for P in poses]
+    parts = []
+    for b in range(0, len(poses), 16):  # ray casts in parallel, 16 keyframes at a time
+        batch = poses[b:b + 16]
+        for P, r in zip(batch, _render_keyframes(L, batch, width, height, f)):
+            parts.append(_surfels_from_keyframe(L, P, width, height, f, rng, rendered=r))
     vw, vh, vf = view_width or width, view_height or height, view_f or f
     vidx = list(range(n_keyframes)) if n_views is None else \
         [int(round(i * (n_keyframes - 1) / max(n_views - 1, 1))) for i in range(n_views)]

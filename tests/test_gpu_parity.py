@@ -13,11 +13,18 @@ import oracle
 from paper_2604_03092_gb300 import _abi, scenes
 from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer, render
 
-from gpu_utils import FWD_ATOL, GRAD_REL_L2, gpu_forward, oracle_cfg, rel_l2, to_dev, upstream, view_stack
+from gpu_utils import (FWD_ATOL, GRAD_REL_L2, MAX_UNRESOLVED, gpu_forward, oracle_cfg, rel_l2, to_dev,
+                       unresolved_flagged, upstream, view_stack)
 
 pytestmark = pytest.mark.gpu
 
-MAX_FLAGGED = 2e-3  # fraction of pixels whose decisions are within rounding
+# Fraction of pixels whose decisions the oracle reports as within rounding,
+# bounded just above the rates measured on these scenes with the oracle
+# alone: one pixel in 12,288 on the random scenes, 2.4e-4 to 3.5e-4 on the
+# 512x384 keyframe views, 9e-4 with the ray-depth option (whose tie between
+# the two terms of the low-pass max is reported too).  Flagged pixels are
+# then checked against either outcome of their decisions.
+MAX_FLAGGED = 5e-4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -168,10 +175,15 @@ def test_bin_sort_long_buckets_and_equal_depths(n, tile):
 # --------------------------------------------------------------------------
 
 def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1, extra_flags=0):
+    """Every pixel of the listed views: within FWD_ATOL of the oracle where
+    its decisions are clear of rounding; where the oracle flags one (at most
+    max_flagged of the pixels), within FWD_ATOL of one of the oracle's
+    outcomes of the flagged decisions (at most MAX_UNRESOLVED of the pixels
+    match none).  Pixels flagged only by `extra_flags` (a tie that switches
+    the ray-depth reading) are excluded and counted with the flagged ones."""
     rast, params, im = gpu_forward(sc, cfg)
     ocfg = oracle_cfg(cfg)
-    flagged = 0
-    total = 0
+    flagged = unresolved = total = 0
     worst = 0.0
     for v in (range(len(sc.views)) if views is None else views):
         p = oracle.preprocess_scene_view(sc, v, ocfg)
@@ -182,9 +194,14 @@ def _check_forward(sc, cfg, views=None, max_flagged=MAX_FLAGGED, mode=1, extra_f
         worst = max(worst, float(err[:, ok].max()))
         assert err[:, ok].max() <= FWD_ATOL, (v, np.unravel_index(np.argmax(np.where(ok, err.max(0), 0)), ok.shape),
                                                err[:, ok].max(axis=1))
+        near = np.flatnonzero((ref.pflags & oracle.PF_FORWARD).reshape(-1) != 0)
+        near = near[(ref.pflags.reshape(-1)[near] & extra_flags) == 0]
+        unresolved += unresolved_flagged(gpu.reshape(8, -1)[:, near], p, near, mode)
         flagged += int((~ok).sum())
         total += ok.size
+    print(f"flagged {flagged}/{total} = {flagged / total:.2e} of pixels; unresolved {unresolved}")
     assert flagged <= max_flagged * total, (flagged, total)
+    assert unresolved <= MAX_UNRESOLVED * total, (unresolved, flagged, total)
     return rast, params, im, worst
 
 
@@ -199,7 +216,8 @@ def test_forward_ray_depth(tile):
     # per-pixel ray-splat intersection depth; a tie between the two terms of
     # the low-pass max flips the depth reading, so such pixels are excluded
     sc = scenes.random_scene(n=4096, seed=7, scale_range=(0.05, 0.3))
-    _check_forward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], depth_ray=True), extra_flags=oracle.PF_BRANCH)
+    _check_forward(sc, RasterConfig(tile_w=tile[0], tile_h=tile[1], depth_ray=True), extra_flags=oracle.PF_BRANCH,
+                   max_flagged=1.2e-3)
 
 
 def test_forward_ray_depth_keyframe_views():
@@ -380,6 +398,15 @@ def test_backward_keyframe_crop():
     _check_backward(sc, RasterConfig())
 
 
+def test_backward_keyframe_full_view():
+    """Whole-image gradient parity on one full 512x384 view of the per-pixel
+    keyframe workload (196,608 surfels; a random upstream gradient at every
+    pixel of every output channel), in the keyframe bucket's launch shape."""
+    sc = scenes.keyframe_scene(seed=1001)
+    sc.views = [sc.views[3]]
+    print(_check_backward(sc, RasterConfig(), seed=11))
+
+
 def test_autograd_function_and_refinement():
     """The autograd.Function gives the same gradients as the direct calls,
     and an Adam refinement of a perturbed keyframe lowers an L1 loss."""
@@ -413,6 +440,21 @@ def test_autograd_function_and_refinement():
             noisy[3].clamp_(0.01, 0.99)
         losses.append(float(loss))
     assert losses[-1] < 0.8 * losses[0], losses
+
+
+def test_second_render_refuses_stale_backward():
+    """A second forward on the same rasterizer overwrites the workspace the
+    first render's backward needs: that backward raises, and the second
+    render's backward (whose state is current) still works."""
+    sc = scenes.random_scene(n=1000, seed=12)
+    params = [p.clone().requires_grad_(True) for p in to_dev(sc)]
+    rast = Rasterizer(sc.views, sc.n, RasterConfig())
+    first = render(rast, *params)
+    second = render(rast, *params)
+    with pytest.raises(RuntimeError, match="another forward"):
+        first[0].sum().backward(retain_graph=True)
+    second[0].sum().backward()
+    assert params[4].grad is not None and torch.count_nonzero(params[4].grad) > 0
 
 
 def test_cuda_graph_replay_matches_eager():

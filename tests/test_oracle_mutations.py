@@ -26,6 +26,9 @@ MUTATIONS = [
     ("low-pass width", "(dx * dx + dy * dy) / (cfg->sigma_lp * cfg->sigma_lp)",
      "(dx * dx + dy * dy) / (2 * cfg->sigma_lp * cfg->sigma_lp)"),
     ("rect too small", "double lo = fmin(fmin(r1, r2), c0 - rlp)", "double lo = fmin(fmin(r1, r2), c0 - rlp) + 0.3"),
+    ("rect too wide", "double lo = fmin(fmin(r1, r2), c0 - rlp)", "double lo = fmin(fmin(r1, r2), c0 - rlp) - 0.3"),
+    ("low-pass square too wide", "double rlp = cfg.sigma_lp * kk;", "double rlp = 2.0 * cfg.sigma_lp * kk;"),
+    ("dual conic root with a spare margin", "double r1 = (di2 + sqrt(disc)) / d22", "double r1 = (di2 + 1.02 * sqrt(disc)) / d22"),
     ("opacity-aware extent", "double k2 = 2.0 * log(op / cfg.alpha_min);", "double k2 = 1.5 * log(op / cfg.alpha_min);"),
     ("homogeneous divide gradient", "dcc = -(b->e.u * du + b->e.v * dv) / c;", "dcc = -(b->e.u * du - b->e.v * dv) / c;"),
     ("ray depth: divide term of its gradient", "g[R_A + 6 + j] -= dz * zi / c * x[j];",

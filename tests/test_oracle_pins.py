@@ -359,6 +359,150 @@ def test_weights_and_permutation():
     assert np.array_equal(im.out, im2.out)
 
 
+# --------------------------------------------------------------------------
+# the screen extent is the bounding box of the alpha >= alpha_min region,
+# no wider: pinned against a closed form and against the projected disk
+# --------------------------------------------------------------------------
+
+def _pix_interval(lo, hi, lim):
+    """Pixel centers (index + 1/2) inside [lo, hi], clipped to [0, lim]."""
+    a, b = int(np.ceil(lo - 0.5)), int(np.floor(hi - 0.5))
+    return max(a, 0), min(b, lim)
+
+
+def _edge_clear(lo, hi, margin=1e-6):
+    """Neither edge of [lo, hi] is within `margin` of a pixel-center boundary."""
+    return all(abs(e - 0.5 - np.round(e - 0.5)) > margin for e in (lo, hi))
+
+
+@pytest.mark.parametrize("fy", [52.0, 71.0])
+def test_extent_fronto_parallel_closed_form(fy):
+    """C5 for a surfel parallel to the image plane: the support of alpha >=
+    alpha_min is the ellipse of Eq. 1's screen-space covariance
+    Sigma = J R2 diag(s^2) R2^T J (J = diag(fx, fy)/z) at Mahalanobis radius
+    k = sqrt(2 ln(sigma/alpha_min)), united with the low-pass disk of radius
+    sigma_lp k around the projected center c; its bounding box is
+    c +- k sqrt(Sigma_ii) and c +- sigma_lp k, and the pixel rect is the
+    pixel centers inside it, clipped to the image -- exactly, so an extent
+    that is wider than the support (a spare margin, a wider low-pass square)
+    fails here as surely as one that is too small."""
+    W, H, fx = 64, 48, 52.0
+    view = _view(W=W, H=H, f=fx, fy=fy)
+    cfg = oracle.Config()
+    rng = np.random.default_rng(int(fy))
+    n = 400
+    z = rng.uniform(1.5, 4.0, n)
+    mu = np.stack([rng.uniform(-1.2, 1.2, n) * z / 2.0, rng.uniform(-0.9, 0.9, n) * z / 2.0, z], 1)
+    th = rng.uniform(0, 2 * np.pi, n)
+    q = np.stack([np.cos(th / 2), np.zeros(n), np.zeros(n), np.sin(th / 2)], 1)
+    # small surfels (the low-pass disk decides) to large ones (the ellipse decides)
+    sc_ = np.exp(rng.uniform(np.log(0.003), np.log(0.15), (n, 2)))
+    op = rng.uniform(0.02, 1.0, n)
+    p = oracle.preprocess(mu.astype(np.float32), sc_.astype(np.float32), q.astype(np.float32),
+                          op.astype(np.float32), np.ones((n, 3), np.float32), view, cfg)
+    m32, s32 = mu.astype(np.float32).astype(np.float64), sc_.astype(np.float32).astype(np.float64)
+    q32, o32 = q.astype(np.float32).astype(np.float64), op.astype(np.float32).astype(np.float64)
+    a_min, slp = float(np.float32(cfg.alpha_min)), float(np.float32(cfg.sigma_lp))
+    fxx, fyy, cxx, cyy = (float(np.float32(x)) for x in (view.fx, view.fy, view.cx, view.cy))
+    checked = lowpass_decides = 0
+    for i in range(n):
+        R2 = _rot(q32[i])[:2, :2]
+        J = np.diag([fxx, fyy]) / m32[i, 2]
+        Sig = J @ R2 @ np.diag(s32[i] ** 2) @ R2.T @ J
+        k = np.sqrt(2.0 * np.log(o32[i] / a_min))
+        c = np.array([fxx * m32[i, 0] / m32[i, 2] + cxx, fyy * m32[i, 1] / m32[i, 2] + cyy])
+        half = np.maximum(k * np.sqrt(np.diag(Sig)), slp * k)
+        lo, hi = c - half, c + half
+        if not (_edge_clear(lo[0], hi[0]) and _edge_clear(lo[1], hi[1])):
+            continue
+        x0, x1 = _pix_interval(lo[0], hi[0], W - 1)
+        y0, y1 = _pix_interval(lo[1], hi[1], H - 1)
+        if x0 > x1 or y0 > y1:
+            assert p.status[i] == oracle.ST_EMPTY, i
+            continue
+        assert p.status[i] == oracle.ST_VISIBLE, i
+        assert list(p.pixrect[i]) == [x0, y0, x1, y1], (i, list(p.pixrect[i]), [x0, y0, x1, y1])
+        checked += 1
+        lowpass_decides += int(np.any(k * np.sqrt(np.diag(Sig)) < slp * k))
+    assert checked > 250 and lowpass_decides > 20, (checked, lowpass_decides)
+
+
+def _disk_extent(mc, U, V, k, f, cc, axis, sign, samples=4096):
+    """max over the boundary circle u^2 + v^2 = k^2 of sign * (projected
+    coordinate along `axis`): P(phi) = mu_c + k (cos phi U + sin phi V),
+    x(phi) = f P_axis / P_z + c; dense sampling, then a bounded scalar
+    refinement around the best sample."""
+    from scipy.optimize import minimize_scalar
+
+    def x(ph):
+        P = mc[:, None] + k * (np.cos(ph) * U[:, None] + np.sin(ph) * V[:, None])
+        return sign * (f * P[axis] / P[2] + cc)
+    ph = np.linspace(0, 2 * np.pi, samples, endpoint=False)
+    j = int(np.argmax(x(ph)))
+    h = 2 * np.pi / samples
+    r = minimize_scalar(lambda t: -float(x(np.array([t]))[0]), bounds=(ph[j] - h, ph[j] + h), method="bounded",
+                        options={"xatol": 1e-13})
+    return sign * max(-r.fun, float(x(ph[j:j + 1])[0]))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_extent_is_bounding_box_of_alpha_support(seed):
+    """C5 for tilted surfels under a general pose: the oracle's extent (a
+    dual conic) equals the bounding box of the set where sigma G >= alpha_min
+    -- the perspective image of the disk u^2 + v^2 <= k^2 on the surfel
+    plane, whose extreme coordinates lie on its boundary circle (found here
+    by maximising the projected circle directly), united with the low-pass
+    disk |x - c| <= sigma_lp k -- and the pixel rect is the pixel centers in
+    it, clipped to the image: no pixel center is in the rect that no point of
+    the support reaches in that row or column."""
+    rng = np.random.default_rng(300 + seed)
+    Rc = Rotation.from_rotvec(rng.normal(size=3) * 0.3).as_matrix()
+    tc = rng.normal(size=3) * 0.3
+    Rt = np.concatenate([Rc, tc[:, None]], 1).astype(np.float32)
+    W, H = 80, 60
+    view = _view(W=W, H=H, f=60.0, Rt=Rt, fy=66.0)
+    cfg = oracle.Config()
+    n = 300
+    R32, t32 = Rt[:, :3].astype(np.float64), Rt[:, 3].astype(np.float64)
+    mc = np.stack([rng.uniform(-1.0, 1.0, n), rng.uniform(-0.8, 0.8, n), rng.uniform(1.5, 4.0, n)], 1)
+    mc[:, :2] *= mc[:, 2:3] / 2.0
+    mu = (mc - t32) @ R32  # world centers: R^T (mc - t)
+    q = rng.normal(size=(n, 4))
+    sc_ = np.exp(rng.uniform(np.log(0.004), np.log(0.2), (n, 2)))
+    op = rng.uniform(0.02, 1.0, n)
+    p = oracle.preprocess(mu.astype(np.float32), sc_.astype(np.float32), q.astype(np.float32),
+                          op.astype(np.float32), np.ones((n, 3), np.float32), view, cfg)
+    m32, s32 = mu.astype(np.float32).astype(np.float64), sc_.astype(np.float32).astype(np.float64)
+    q32, o32 = q.astype(np.float32).astype(np.float64), op.astype(np.float32).astype(np.float64)
+    a_min, slp = float(np.float32(cfg.alpha_min)), float(np.float32(cfg.sigma_lp))
+    fxx, fyy, cxx, cyy = (float(np.float32(x)) for x in (view.fx, view.fy, view.cx, view.cy))
+    checked = 0
+    for i in range(n):
+        if p.status[i] not in (oracle.ST_VISIBLE, oracle.ST_EMPTY) or p.sflags[i]:
+            continue
+        Rs = _rot(q32[i])
+        mcam = R32 @ m32[i] + t32
+        U = R32 @ Rs[:, 0] * s32[i, 0]
+        V = R32 @ Rs[:, 1] * s32[i, 1]
+        k = np.sqrt(2.0 * np.log(o32[i] / a_min))
+        c = np.array([fxx * mcam[0] / mcam[2] + cxx, fyy * mcam[1] / mcam[2] + cyy])
+        lo, hi = np.zeros(2), np.zeros(2)
+        for ax, (f_, cc) in enumerate(((fxx, cxx), (fyy, cyy))):
+            hi[ax] = max(_disk_extent(mcam, U, V, k, f_, cc, ax, 1.0), c[ax] + slp * k)
+            lo[ax] = min(_disk_extent(mcam, U, V, k, f_, cc, ax, -1.0), c[ax] - slp * k)
+        if not (_edge_clear(lo[0], hi[0], 1e-5) and _edge_clear(lo[1], hi[1], 1e-5)):
+            continue
+        x0, x1 = _pix_interval(lo[0], hi[0], W - 1)
+        y0, y1 = _pix_interval(lo[1], hi[1], H - 1)
+        if x0 > x1 or y0 > y1:
+            assert p.status[i] == oracle.ST_EMPTY, i
+            continue
+        assert p.status[i] == oracle.ST_VISIBLE, i
+        assert list(p.pixrect[i]) == [x0, y0, x1, y1], (i, list(p.pixrect[i]), [x0, y0, x1, y1], lo, hi)
+        checked += 1
+    assert checked > 150, checked
+
+
 @pytest.mark.parametrize("seed,tile", [(0, (16, 16)), (1, (8, 8)), (2, (32, 8))])
 def test_binned_equals_definition(seed, tile):
     """P6: restricting each surfel to the pixels of its opacity-aware rect
