@@ -168,6 +168,12 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   // the records in sorted-list order, written by the forward as it stages
   // them and read back contiguously by the backward
   L->rcopy = take(sizeof(float4) * REC_F4 * (size_t)L->cap);
+  // per (32-entry word of a tile's list, pixel of the tile): the entries of
+  // the word the forward blended at that pixel, read by the backward.  Tile
+  // t's words start at range.x / 32 + t, so cap / 32 + T + 1 words cover
+  // every tile whatever its range.
+  L->bmask_words = L->cap / 32 + T + 1;
+  L->bmask = take(sizeof(uint32_t) * (size_t)L->bmask_words * (size_t)cfg->tile_w * (size_t)cfg->tile_h);
   L->total = off;
   return true;
 }

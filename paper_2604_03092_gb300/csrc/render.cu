@@ -121,6 +121,12 @@ struct RenderArgs {
   const uint32_t* vals;
   const float4* records;
   float4* rcopy;  // records in sorted-list order (instance i at i * REC_F4)
+  // Blended-pair masks: for tile t, word w of its list (entries range.x +
+  // 32 w ...) and the pixel of forward thread k, the entries of the word the
+  // forward blended there, at ((range.x / 32 + t + w) * NT + k).  Written by
+  // the forward for every chunk it stages, read by the backward.
+  uint32_t* bmask;
+  int64_t bmask_words;
   float* rgrad;
   RastParams P;
   Header* hdr;
@@ -338,6 +344,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     const bool inside = ipx < vw.W && ipy < vw.H;
     const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
+    const int64_t woff = (int64_t)(range.x >> 5) + t;  // this tile's first blended-mask word
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
     uint32_t last = range.x;
     bool done = !inside;
@@ -345,6 +352,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int n_act = __syncthreads_count(!done);
       if (n_act == 0) break;
       const int count = (int)min64(CHUNK, (int64_t)range.y - base);
+      const int nwd = (count + 31) >> 5;
+      uint32_t* bm = A.bmask + (woff + ((base - (int64_t)range.x) >> 5)) * NT + threadIdx.x;
+      const bool bm_ok = s2d_check(woff + ((base - (int64_t)range.x) >> 5) + nwd <= A.bmask_words, A.hdr);
       if (threadIdx.x == 0) {
         S.nact = 0;
         S.next = 0;
@@ -354,13 +364,20 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       __syncthreads();
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
-        if (__all_sync(0xffffffffu, done)) continue;
-        const int nwd = (count + 31) >> 5;
+        if (__all_sync(0xffffffffu, done)) {
+          for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(int64_t)w2 * NT] = 0u;
+          continue;
+        }
         for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
         int wd = 0;
         uint32_t b = done ? 0u : S.bits[wid][0][lane];
+        uint32_t bl = 0u;  // entries of word wd this pixel blended (word wd's slot takes them when the walk moves on)
         for (;;) {
-          while (b == 0 && !done && wd + 1 < nwd) b = S.bits[wid][++wd][lane];
+          while (b == 0 && !done && wd + 1 < nwd) {
+            S.bits[wid][wd][lane] = bl;
+            bl = 0u;
+            b = S.bits[wid][++wd][lane];
+          }
           const bool has = b != 0 && !done;
           if (!__any_sync(0xffffffffu, has)) break;
           if (!has) continue;
@@ -388,8 +405,12 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           N2 = __fmaf_rn(w, nrm.z, N2);
           T = Tn;
           last = (uint32_t)(base + j + 1);
+          bl |= 1u << (j & 31);
           n_blend++;
         }
+        S.bits[wid][wd][lane] = bl;
+        for (int w2 = wd + 1; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;
+        for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(int64_t)w2 * NT] = S.bits[wid][w2][lane];
       } else {
         // ---- tail: warps pull the remaining pixels; a warp composites 32 of
         //      a pixel's entries per step with a prefix product of (1 - alpha)
@@ -398,6 +419,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           S.apix[k] = (uint16_t)threadIdx.x;
           S.st[threadIdx.x] = FwdState{T, C0, C1, C2, D, N0, N1, N2, last, 0u};
         }
+        for (int w2 = 0; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;  // blended entries, set below
         __syncthreads();
         for (;;) {
           int k = 0;
@@ -454,6 +476,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
             for (int q = 0; q < 7; q++) acc[q] += vals[q];
             n_eval += (has && lane <= sl) ? 1u : 0u;
             n_blend += contrib ? 1u : 0u;
+            if (contrib) atomicOr(&S.bits[pw][j >> 5][pl], 1u << (j & 31));
             const uint32_t cb = __ballot_sync(0xffffffffu, contrib);
             if (cb) lst = (uint32_t)(base + __shfl_sync(0xffffffffu, j, 31 - __clz(cb)) + 1);
             if (stopb) {
@@ -468,6 +491,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           __syncwarp();
         }
         __syncthreads();
+        for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(int64_t)w2 * NT] = S.bits[wid][w2][lane];
         if (!done) {
           const FwdState st = S.st[threadIdx.x];
           T = st.T; C0 = st.C0; C1 = st.C1; C2 = st.C2; D = st.D;
@@ -700,25 +724,29 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     if (my_last > range.x) atomicMax(&S.top, my_last);
     __syncthreads();
     const uint32_t top = S.top;
-    for (int64_t hi = top; hi > (int64_t)range.x; hi -= CHUNK) {
-      const int64_t lo = max64((int64_t)range.x, hi - CHUNK);
-      const int count = (int)(hi - lo);
+    // chunks start at multiples of CHUNK from the tile's first entry, so that
+    // they cover whole words of the forward's blended-pair masks; the deepest
+    // one ends at the tile's largest `last`
+    const int64_t woff = (int64_t)(range.x >> 5) + t;
+    const int nch = (int)(((int64_t)top - (int64_t)range.x + CHUNK - 1) / CHUNK);
+    for (int k = nch - 1; k >= 0; k--) {
+      const int64_t lo = (int64_t)range.x + (int64_t)k * CHUNK;
+      const int count = (int)(min64(lo + CHUNK, (int64_t)top) - lo);
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
       const int64_t nlo = max64((int64_t)range.x, lo - CHUNK);  // the chunk in front, processed next
       stage_chunk_seq<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
-      __syncthreads();
-      // per-pixel masks of this chunk, restricted to the entries below the pixel's last
-      const int lim = act ? (int)min64((int64_t)my_last - lo, count) : 0;
+      // per-pixel masks of this chunk: the entries the forward blended at the pixel
       {
+        const int64_t w0 = woff + ((lo - (int64_t)range.x) >> 5);
+        const bool bm_ok = s2d_check(w0 + nwd <= A.bmask_words, A.hdr);
+        const uint32_t* bm = A.bmask + w0 * NT + threadIdx.x;
         int pc[NWD];
 #pragma unroll
         for (int wd = 0; wd < NWD; wd++) {
           uint32_t m = 0;
           if (wd < nwd) {
-            m = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
-            const int keep = lim - wd * 32;
-            m = keep >= 32 ? m : (keep <= 0 ? 0u : (m & ((1u << keep) - 1u)));
+            m = (act && bm_ok) ? __ldg(bm + (int64_t)wd * NT) : 0u;
             S.pbits[myslot][wd] = m;
           }
           pc[wd] = __popc(m);
@@ -1031,6 +1059,8 @@ static RenderArgs make_args(const Layout& L, const RastParams& P, char* ws, cons
   A.vals = vals;
   A.records = reinterpret_cast<const float4*>(ws + L.records);
   A.rcopy = reinterpret_cast<float4*>(ws + L.rcopy);
+  A.bmask = reinterpret_cast<uint32_t*>(ws + L.bmask);
+  A.bmask_words = L.bmask_words;
   A.rgrad = reinterpret_cast<float*>(ws + L.rgrad);
   A.P = P;
   A.hdr = reinterpret_cast<Header*>(ws + L.header);

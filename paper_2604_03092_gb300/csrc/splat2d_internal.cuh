@@ -89,7 +89,8 @@ constexpr float kLn2 = 0.69314718055994531f;
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t header, views, groups, ntiles, records, rgrad, keys0, keys1, vals0, vals1, sort_hist, ranges,
-      tile_count, tile_order, tile_hist, tile_class, tfinal, last, rcopy, total;
+      tile_count, tile_order, tile_hist, tile_class, tfinal, last, rcopy, bmask, total;
+  int64_t bmask_words;  // 32-entry words of blended-pair masks (each holds one word per tile pixel)
   int64_t R, T, P, cap;
   int64_t n_work;     // sum over view groups of the surfel range sizes
   int32_t V, G;
