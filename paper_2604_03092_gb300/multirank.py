@@ -7,6 +7,13 @@ only collectives are the timing reductions below (a barrier around the
 timed region, the maximum of the per-rank times, and the sum of the views
 the ranks rendered), which run after the timed region ends.
 
+A second partition splits the views of ONE submap across ranks: every rank
+holds all of the submap's surfels, renders its own contiguous share of the
+views forward and backward, and the ranks then sum their surfel-parameter
+gradients (one all-reduce of d_params [N, 13]: means 3, scales 2, quats 4,
+opacity 1, rgb 3); the per-view pose gradients stay with the rank that owns
+the view.  `view_shard` and `allreduce_surfel_grads` are that exchange.
+
 The functions take the process group's backend as it is (NCCL on GPUs, gloo
 in the CPU tests), so the same code is exercised in both.
 """
@@ -73,3 +80,39 @@ def whole_job_rate(units_all_ranks: float, max_elapsed_ms: float) -> float:
     if max_elapsed_ms <= 0.0:
         raise ValueError("elapsed time must be positive")
     return units_all_ranks / (max_elapsed_ms / 1e3)
+
+
+def view_shard(n_views: int, rank: int, world: int) -> range:
+    """The views of one submap that `rank` renders when its views are split
+    across `world` ranks: contiguous, sizes differing by at most one."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError(f"bad rank {rank} of world size {world}")
+    q, r = divmod(int(n_views), world)
+    lo = rank * q + min(rank, r)
+    return range(lo, lo + q + (1 if rank < r else 0))
+
+
+SURFEL_GRAD_FIELDS = (("means", 3), ("scales", 2), ("quats", 4), ("opacity", 1), ("rgb", 3))
+
+
+def allreduce_surfel_grads(grads) -> None:
+    """Sum, in place and over all ranks, the surfel-parameter gradients of
+    ranks that rendered disjoint views of the same surfels: the five arrays
+    (any object with tensor attributes means [N,3], scales [N,2], quats
+    [N,4], opacity [N], rgb [N,3] of one dtype and device) are packed into
+    one [N, 13] buffer, all-reduced with a sum, and unpacked.  The pose
+    gradients are per view and are not exchanged.  A no-op on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return
+    parts = [getattr(grads, name).reshape(-1, k) for name, k in SURFEL_GRAD_FIELDS]
+    n = parts[0].shape[0]
+    if any(p.shape[0] != n for p in parts):
+        raise ValueError("surfel gradient arrays disagree on the surfel count")
+    flat = torch.cat(parts, 1).contiguous()
+    dist.all_reduce(flat, op=dist.ReduceOp.SUM)
+    col = 0
+    for (name, k), p in zip(SURFEL_GRAD_FIELDS, parts):
+        p.copy_(flat[:, col:col + k])
+        col += k
