@@ -253,6 +253,65 @@ def _recorded_traffic(stage: str, cfg, n_inst: int):
         return None
 
 
+def _time_refinement(rast, params, sc, dev, iters: int):
+    """The refinement loop the rasterizer serves: `iters` Adam iterations of
+    L1 RGB + 0.1 L1 depth against the keyframes' ray-cast targets over all
+    views, through the differentiable render (Splat2DRender), every surfel
+    parameter and every view's pose tangent optimised.  The surfels start
+    from the workload with perturbed colours and opacities.  Times the loop
+    (render, loss, backward, Adam step, clamps) with CUDA events after three
+    untimed iterations; the loss is kept on the device every tenth iteration
+    and read once at the end."""
+    import torch
+
+    from paper_2604_03092_gb300 import _abi
+    from paper_2604_03092_gb300.rasterizer import render
+
+    g = torch.Generator(device=dev).manual_seed(7)
+    prm = [p.detach().clone() for p in params]
+    prm[4] = (prm[4] + 0.1 * torch.randn(prm[4].shape, device=dev, generator=g)).clamp_(0.0, 1.0)
+    prm[3] = prm[3] * (0.8 + 0.2 * torch.rand(prm[3].shape, device=dev, generator=g))
+    prm = [p.requires_grad_(True) for p in prm]
+    pose = torch.zeros(rast.n_views, 6, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([{"params": [prm[0]], "lr": 1e-4}, {"params": [prm[1]], "lr": 1e-5},
+                            {"params": [prm[2]], "lr": 1e-3}, {"params": [prm[3]], "lr": 1e-2},
+                            {"params": [prm[4]], "lr": 1e-2}])
+    trgb = torch.from_numpy(sc.target_rgb).to(dev)
+    tdep = torch.from_numpy(sc.target_depth).to(dev)
+    rast.set_capacity(int(rast.capacity * 1.2))  # room for the instance count to grow as the surfels move
+    losses = []
+
+    def it(k):
+        opt.zero_grad(set_to_none=False)
+        rgb, depth, _, _ = render(rast, *prm, pose_tangent=pose, check=False)
+        loss = (rgb - trgb).abs().mean() + 0.1 * (depth - tdep).abs().mean()
+        loss.backward()
+        opt.step()
+        with torch.no_grad():
+            prm[3].clamp_(0.01, 0.99)
+            prm[1].clamp_(min=1e-6)
+        if k % 10 == 0:
+            losses.append(loss.detach())
+
+    for k in range(3):
+        it(-1)
+    torch.cuda.synchronize()
+    losses.clear()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for k in range(iters):
+        it(k)
+    b.record()
+    torch.cuda.synchronize()
+    status = rast.status()
+    ms = a.elapsed_time(b) / iters
+    return {"iterations": iters, "ms_per_iter": ms, "views_per_s": rast.n_views / (ms / 1e3),
+            "loss_every_10": [float(x) for x in losses], "status": int(status),
+            "status_ok": status == _abi.OK,
+            "note": "Adam over means, scales, quats, opacity, rgb and every view's pose tangent; L1 RGB + 0.1 L1 "
+                    "depth against the ray-cast keyframe targets; colours and opacities perturbed at the start"}
+
+
 def _time_maintenance(rast, params, sc, out, dev, hbm_gbs, reps: int = 5):
     """CUDA-event times of the map-maintenance kernels on this workload:
     error attribution over all views (after a forward), the accumulation
@@ -320,7 +379,9 @@ def main():
     ap.add_argument("--fwd-tail", type=int, default=None, help="forward tail threshold per warp (255 = always)")
     ap.add_argument("--bwd-chunk", type=int, default=None, help="chunk of the backward pass (default: --chunk)")
     ap.add_argument("--plain-steps", type=int, default=2, help="steps of the per-view plain-launch baseline (0=skip)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--refine-iters", type=int, default=100,
+                    help="Adam iterations of the refinement loop through Splat2DRender (0 = skip)")
     ap.add_argument("--cpu-views", type=int, default=4, help="whole views the oracle CPU baseline renders (~3 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-maintenance", action="store_true", help="skip timing the map-maintenance kernels")
@@ -386,12 +447,12 @@ def main():
     grads = rast.new_grads()
     stages = ["preprocess", "bin_sort", "render_fwd", "render_bwd", "preprocess_bwd"]
 
-    def step(ev=None):
-        for t in grads:
+    def step(ev=None, prm=params, grd=grads):
+        for t in grd:
             t.zero_()
         if ev is not None:
             ev[0].record()
-        rast.preprocess(*params)
+        rast.preprocess(*prm)
         if ev is not None:
             ev[1].record()
         rast.bin_sort()
@@ -403,7 +464,7 @@ def main():
         rast.render_bwd_tiles(d_out)
         if ev is not None:
             ev[4].record()
-        rast.preprocess_bwd(*params, grads)
+        rast.preprocess_bwd(*prm, grd)
         if ev is not None:
             ev[5].record()
 
@@ -511,25 +572,61 @@ def main():
         del singles
 
     # ---- end to end through the public API with host buffers -----------------
+    # Every step copies its inputs (the surfel parameters) from pinned host
+    # memory and reads its result (the parameter and pose gradients) back.
+    # The copies run on a second stream and are double-buffered: step k+1's
+    # parameters go up while step k computes, and step k's gradients come
+    # down while step k+1 computes; events order each buffer's uses.
     pinned_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
                  (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
-    pinned_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in grads]
+    pinned_out = [[torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in grads] for _ in range(2)]
     h2d = sum(t.numel() * t.element_size() for t in pinned_in)
-    d2h = sum(t.numel() * t.element_size() for t in pinned_out)
+    d2h = sum(t.numel() * t.element_size() for t in pinned_out[0])
+    prm_b = [params, [torch.empty_like(t) for t in params]]
+    grd_b = [grads, rast.new_grads()]
+    comp = torch.cuda.current_stream()
+    copy_s = torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]    # parameters of buffer b are on the device
+    ev_comp = [torch.cuda.Event() for _ in range(2)]  # the step that used buffer b has finished
+    ev_out = [torch.cuda.Event() for _ in range(2)]   # gradients of buffer b have reached the host
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.e2e_steps):
-        for dst, src in zip(params, pinned_in):
+    a.record(comp)
+    copy_s.wait_stream(comp)
+    with torch.cuda.stream(copy_s):
+        for dst, src in zip(prm_b[0], pinned_in):
             dst.copy_(src, non_blocking=True)
-        step()
-        for dst, src in zip(pinned_out, grads):
-            dst.copy_(src, non_blocking=True)
-    b.record()
+        ev_in[0].record(copy_s)
+    for k in range(args.e2e_steps):
+        bi = k % 2
+        comp.wait_event(ev_in[bi])
+        if k >= 2:
+            comp.wait_event(ev_out[bi])  # buffer bi's gradients from step k-2 have been read
+        step(prm=prm_b[bi], grd=grd_b[bi])
+        ev_comp[bi].record(comp)
+        with torch.cuda.stream(copy_s):
+            if k + 1 < args.e2e_steps:
+                if k >= 1:
+                    copy_s.wait_event(ev_comp[1 - bi])  # step k-1 no longer reads buffer 1-bi
+                for dst, src in zip(prm_b[1 - bi], pinned_in):
+                    dst.copy_(src, non_blocking=True)
+                ev_in[1 - bi].record(copy_s)
+            copy_s.wait_event(ev_comp[bi])
+            for dst, src in zip(pinned_out[bi], grd_b[bi]):
+                dst.copy_(src, non_blocking=True)
+            ev_out[bi].record(copy_s)
+    comp.wait_stream(copy_s)
+    b.record(comp)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b)
     e2e_vps = multirank.whole_job_rate(multirank.sum_over_ranks(V * args.e2e_steps, dev),
                                        multirank.max_over_ranks(e2e_ms, dev))
+    del prm_b, grd_b
+
+    # ---- the refinement loop (Sec. 4.3, "Lightweight Map Refinement") --------
+    refine = None
+    if args.refine_iters > 0 and rank == 0 and sc.target_rgb is not None and rast.uniform:
+        refine = _time_refinement(rast, params, sc, dev, args.refine_iters)
 
     # ---- map maintenance around the refinement (Sec. 4.3), on this workload ---
     maint = None
@@ -623,6 +720,7 @@ def main():
             "pairs": {k: st[k] for k in ("fwd_pairs_evaluated", "fwd_pairs_blended", "bwd_pairs_evaluated",
                                          "bwd_pairs_blended", "bwd_terms_outside")},
             "cpu_baseline": cpu,
+            "refinement": refine,
             "map_maintenance": maint,
         }
         print(json.dumps(line), flush=True)

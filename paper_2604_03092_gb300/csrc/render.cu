@@ -22,8 +22,6 @@
 // atomics per (tile, entry) moves the sums to the gradient record.
 #include <cuda_runtime.h>
 
-#include <type_traits>
-
 #include "splat2d_internal.cuh"
 
 namespace s2d {
@@ -106,6 +104,12 @@ __device__ __forceinline__ void eval_pair(const float4 c, const float4 p, const 
 // is z p22 / c.
 __device__ __forceinline__ float pair_depth(const Pair& e, float z, float p22, int depth_ray) {
   return (depth_ray && e.obj) ? z * p22 * e.rc : z;
+}
+
+// Whether the tile-relative pixel (lx, ly) lies in a packed clipped rect.
+__device__ __forceinline__ bool in_tile_rect(uint32_t r, int lx, int ly) {
+  return lx >= (int)(r & 0xffu) && ly >= (int)((r >> 8) & 0xffu) && lx <= (int)((r >> 16) & 0xffu) &&
+         ly <= (int)(r >> 24);
 }
 
 struct RenderArgs {
@@ -244,48 +248,84 @@ __device__ __forceinline__ int nth_set_bit(uint32_t b, int r) {
   return pos;
 }
 
-// Positions of a warp's pair stream whose weights are kept between the two
-// passes of the forward (four steps of 32).
-constexpr int FWD_BLK = 128;
+// Sum 8 per-lane values over the warp and give every lane all 8 totals
+// (a transposing butterfly: each level halves the values a lane keeps).
+__device__ __forceinline__ void warp_sum8_all(float (&v)[8], int lane) {
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    const bool up = lane & 16;
+    const float send = up ? v[i] : v[i + 4];
+    const float keep = up ? v[i + 4] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; i++) {
+    const bool up = lane & 8;
+    const float send = up ? v[i] : v[i + 2];
+    const float keep = up ? v[i + 2] : v[i];
+    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const float send = up ? v[0] : v[1];
+    const float keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+  // lane L now holds the total of value index (L >> 2) & 7
+  const float t0 = v[0];
+#pragma unroll
+  for (int k = 0; k < 8; k++) v[k] = __shfl_sync(0xffffffffu, t0, k << 2);
+}
 
-// Dynamic shared memory of the forward kernel.  Per-pixel arrays are
-// indexed by the pixel's thread (each thread owns one pixel of the tile).
+// Warp-wide inclusive scans over lanes.
+__device__ __forceinline__ float warp_scan_mul(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = __fmul_rn(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_scan_add(float x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const float y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Per-pixel state of the forward while it is handed between warps.
+struct FwdState {
+  float T, C0, C1, C2, D, N0, N1, N2;
+  uint32_t last, done;
+};
+
+// Dynamic shared memory of the forward kernel.
 template <int NT, int CHUNK>
 struct FwdSmem {
   SRecs<CHUNK> rec;
-  uint32_t pbits[NT][CHUNK / 32];  // per pixel: chunk entries whose rect holds it (none once it has stopped)
-  uint16_t pcnt[NT][CHUNK / 32];   // per pixel: set bits in its mask words before word w
-  float tq[NT];                    // per pixel: transmittance in front of its next pair of the stream
-  uint8_t dead[NT];                // per pixel: stopped inside this chunk
-  float sw[NT / 32][FWD_BLK];      // per warp: weight of each pair of the current block (0: not blended)
-  float sz[NT / 32][FWD_BLK];      // per warp: depth each pair contributes (ray-depth option only)
-  using JT = typename std::conditional<(CHUNK > 256), uint16_t, uint8_t>::type;  // holds an entry of the chunk
-  JT sj[NT / 32][FWD_BLK];         // per warp: entry of each pair
-  uint8_t own[NT / 32][32];        // per warp and step: lane of the pixel whose run starts at each position
-  int item;
+  uint32_t bits[NT / 32][CHUNK / 32][32];
+  FwdState st[NT];
+  uint16_t list[NT / 32][CHUNK];
+  uint16_t apix[NT];
+  int item, nact, next;
 };
 
-// Forward compositing over a balanced pair stream.  Per chunk, each warp
-// lays the (pixel, entry) pairs of its 32 pixels end to end -- pixel by
-// pixel, each pixel's entries front to back -- and takes them 32 at a time,
-// so that every lane evaluates a pair on every step whatever the per-pixel
-// counts (a lane-per-pixel walk waits at each chunk for the pixel with the
-// most entries).  Pass 1 evaluates alpha, recovers the transmittance in
-// front of each pair with a segmented prefix product of (1 - alpha) along
-// the pixel's run, finds the pair whose blend would take it below t_min
-// (the pixel stops there) and keeps each pair's weight w = alpha T; pass 2,
-// every four steps, lets each lane add up its own pixel's weighted colour,
-// depth and normal from those weights.
+// Tail mode of the forward: once at most P.fwd_tail pixels of a tile per
+// warp are still compositing, all warps share them, one pixel at a time.
+
 template <int TW, int TH, int CHUNK>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 12) : 3) k_render_fwd(const RenderArgs A) {
-  constexpr int NT = TW * TH, WX = TW / 8, NWD = CHUNK / 32;
+  constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FwdSmem<NT, CHUNK>& S = *reinterpret_cast<FwdSmem<NT, CHUNK>*>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t le_mask = (2u << lane) - 1u;  // lanes <= this lane
+  const uint32_t lt_mask = (1u << lane) - 1u;
   const RastParams& P = A.P;
   uint32_t n_eval = 0, n_blend = 0;
-  uint8_t* own = S.own[wid];
   // a failed binning (instance capacity exceeded) leaves no valid lists
   if (A.hdr->status != 0) return;
   for (;;) {
@@ -302,146 +342,168 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
     const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
     const bool inside = ipx < vw.W && ipy < vw.H;
+    const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
-    const int64_t woff = (int64_t)(range.x >> 5) + t;  // this tile's first blended-mask word
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
     uint32_t last = range.x;
     bool done = !inside;
     for (int64_t base = range.x; base < range.y; base += CHUNK) {
-      if (__syncthreads_count(!done) == 0) break;
+      const int n_act = __syncthreads_count(!done);
+      if (n_act == 0) break;
       const int count = (int)min64(CHUNK, (int64_t)range.y - base);
       const int nwd = (count + 31) >> 5;
-      const int64_t w0 = woff + ((base - (int64_t)range.x) >> 5);
-      const bool bm_ok = s2d_check(w0 + nwd <= A.bmask_words, A.hdr);
+      // this chunk's first blended-mask word (tile t's words start at range.x / 32 + t);
+      // computed where it is written, so nothing of it stays live across the walk
+      auto mask_word = [&]() { return (range.x >> 5) + (uint32_t)t + (uint32_t)((base - (int64_t)range.x) >> 5); };
+      const bool bm_ok = s2d_check((int64_t)mask_word() + nwd <= A.bmask_words, A.hdr);
+      if (threadIdx.x == 0) {
+        S.nact = 0;
+        S.next = 0;
+      }
       stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, base, count, S.rec, nullptr, base + CHUNK,
                              (int)max64(min64(CHUNK, (int64_t)range.y - base - CHUNK), 0), true);
       __syncthreads();
-      // this pixel's entries of the chunk (none once it has stopped)
-      uint32_t cntp = 0;
-#pragma unroll
-      for (int wd = 0; wd < NWD; wd++) {
-        if (wd < nwd) {
-          uint32_t m = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
-          m = done ? 0u : m;
-          S.pbits[threadIdx.x][wd] = m;
-          S.pcnt[threadIdx.x][wd] = (uint16_t)cntp;
-          cntp += __popc(m);
+      if (n_act > P.fwd_tail * NW) {
+        // ---- bulk: each lane walks its own pixel's entries --------------------
+        if (__all_sync(0xffffffffu, done)) {
+          uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
+          for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(size_t)w2 * NT] = 0u;
+          continue;
         }
-      }
-      S.tq[threadIdx.x] = T;
-      S.dead[threadIdx.x] = 0;
-      // this warp's stream: its pixels' pairs end to end
-      uint32_t incl = cntp;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t myoff = incl - cntp;
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      __syncwarp();
-      uint32_t blw[NWD];  // entries of each word this pixel blended
-#pragma unroll
-      for (int wd = 0; wd < NWD; wd++) blw[wd] = 0u;
-      int carry = 0;  // lane of the pixel whose run reaches the previous step's last position
-      for (uint32_t b0 = 0; b0 < total; b0 += FWD_BLK) {
-        const uint32_t bend = min(total, b0 + (uint32_t)FWD_BLK);
-        // ---- pass 1: alpha, transmittance and the stop, 32 pairs per step
-        for (uint32_t sb = b0; sb < bend; sb += 32) {
-          const bool starts_here = cntp > 0 && myoff >= sb && myoff < sb + 32;
-          if (starts_here) own[myoff - sb] = (uint8_t)lane;
-          const uint32_t M = __reduce_or_sync(0xffffffffu, starts_here ? (1u << (myoff - sb)) : 0u);
-          __syncwarp();
-          const bool has = sb + lane < total;
-          const uint32_t below = M & le_mask;
-          const int ol = below ? (int)own[31 - __clz(below)] : carry;
-          carry = __shfl_sync(0xffffffffu, ol, 31);
-          const uint32_t ooff = __shfl_sync(0xffffffffu, myoff, ol);
-          const int ps = wid * 32 + ol;  // the pixel's thread
-          int j = 0;
-          if (has) {
-            // entry: the (q+1)-th set bit of the pixel's mask from the front;
-            // its word is the last w whose preceding count is <= q
-            const int q = (int)(sb + lane - ooff);
-            int wd = 0, cin = 0;
-#pragma unroll
-            for (int h = 0; h < NWD; h++) {
-              const int c = (int)S.pcnt[ps][h];
-              if (h < nwd && c <= q) { wd = h; cin = c; }
-            }
-            j = wd * 32 + nth_set_bit(S.pbits[ps][wd], q - cin + 1);
+        for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
+        int wd = 0;
+        uint32_t b = done ? 0u : S.bits[wid][0][lane];
+        uint32_t bl = 0u;  // entries of word wd this pixel blended (word wd's slot takes them when the walk moves on)
+        for (;;) {
+          while (b == 0 && !done && wd + 1 < nwd) {
+            S.bits[wid][wd][lane] = bl;
+            bl = 0u;
+            b = S.bits[wid][++wd][lane];
           }
-          const bool start = has && (lane == 0 || ((M >> lane) & 1u));
-          const bool end = has && (lane == 31 || sb + lane + 1 == total || ((M >> (lane + 1)) & 1u));
-          const uint32_t starts = __ballot_sync(0xffffffffu, start);
-          const int s0 = 31 - __clz(starts & le_mask);  // first lane of this lane's run in the step
-          const float fx = (float)(bx + (ol & 7)) + 0.5f, fy = (float)(by + (ol >> 3)) + 0.5f;
+          const bool has = b != 0 && !done;
+          if (!__any_sync(0xffffffffu, has)) break;
+          if (!has) continue;
+          const int j = wd * 32 + __ffs(b) - 1;
+          b &= b - 1;
           Pair e;
-          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], fx, fy, P.lp_scale, P.alpha_max, e);
-          const bool kept = has && e.alpha >= P.alpha_min;
-          // segmented prefix product: transmittance behind this pair, relative to the run's start
-          float x = kept ? __fsub_rn(1.f, e.alpha) : 1.f;
-#pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const float y = __shfl_up_sync(0xffffffffu, x, o);
-            x = (lane - o >= s0) ? __fmul_rn(x, y) : x;
+          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], px, py, P.lp_scale, P.alpha_max, e);
+          n_eval++;
+          if (e.alpha < P.alpha_min) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
+          if (Tn < P.t_min) {
+            done = true;
+            continue;
           }
-          float xe = __shfl_up_sync(0xffffffffu, x, 1);
-          xe = (lane == s0) ? 1.f : xe;
-          const float Tin = S.tq[ps];
-          const bool dd = S.dead[ps] != 0;
-          const float Tb = __fmul_rn(Tin, xe), Ta = __fmul_rn(Tin, x);
-          const bool stop = kept && !dd && Ta < P.t_min;
-          const uint32_t SB = __ballot_sync(0xffffffffu, stop) & ~((1u << s0) - 1u);  // stops in runs from s0 on
-          const uint32_t st_upto = SB & le_mask;      // stops of this run at or before this lane
-          const bool contrib = kept && !dd && st_upto == 0u;
-          n_eval += (has && !dd && (st_upto & ~(1u << lane)) == 0u) ? 1u : 0u;
-          n_blend += contrib ? 1u : 0u;
-          const uint32_t pos = sb + lane - b0;
-          if (has) {
-            S.sw[wid][pos] = contrib ? __fmul_rn(e.alpha, Tb) : 0.f;
-            S.sj[wid][pos] = (typename FwdSmem<NT, CHUNK>::JT)j;
-            if (P.depth_ray) S.sz[wid][pos] = pair_depth(e, S.rec.col[j].w, S.rec.q[j].z, 1);
-          }
-          // the run's last lane carries the pixel's transmittance to its next pair
-          // (or, at a stop, keeps the transmittance in front of the stopping pair)
-          const int fs = st_upto ? __ffs(st_upto) - 1 : lane;
-          const float Tstop = __shfl_sync(0xffffffffu, Tb, fs);
-          __syncwarp();
-          if (end && !dd) {
-            S.tq[ps] = st_upto ? Tstop : Ta;
-            if (st_upto) S.dead[ps] = 1;
-          }
-          __syncwarp();
-        }
-        // ---- pass 2: each lane adds up its own pixel's pairs of the block
-        const uint32_t p0 = max(myoff, b0), p1 = min(myoff + cntp, bend);
-        for (uint32_t pp = p0; pp < p1; pp++) {
-          const float w = S.sw[wid][pp - b0];
-          if (w == 0.f) continue;  // a kept pair has w = alpha T >= alpha_min t_min > 0
-          const int j = S.sj[wid][pp - b0];
+          const float w = __fmul_rn(e.alpha, T);
           const float4 col = S.rec.col[j], nrm = S.rec.n[j];
           C0 = __fmaf_rn(w, col.x, C0);
           C1 = __fmaf_rn(w, col.y, C1);
           C2 = __fmaf_rn(w, col.z, C2);
-          D = __fmaf_rn(w, P.depth_ray ? S.sz[wid][pp - b0] : col.w, D);
+          float zp = col.w;
+          if (P.depth_ray) zp = pair_depth(e, col.w, S.rec.q[j].z, 1);
+          D = __fmaf_rn(w, zp, D);
           N0 = __fmaf_rn(w, nrm.x, N0);
           N1 = __fmaf_rn(w, nrm.y, N1);
           N2 = __fmaf_rn(w, nrm.z, N2);
+          T = Tn;
           last = (uint32_t)(base + j + 1);
-#pragma unroll
-          for (int wd = 0; wd < NWD; wd++) blw[wd] |= ((j >> 5) == wd) ? (1u << (j & 31)) : 0u;
+          bl |= 1u << (j & 31);
+          n_blend++;
         }
-        __syncwarp();
-      }
-      if (!done) {
-        T = S.tq[threadIdx.x];
-        done = S.dead[threadIdx.x] != 0;
-      }
-      uint32_t* bm = A.bmask + w0 * NT + threadIdx.x;
+        S.bits[wid][wd][lane] = bl;
+        for (int w2 = wd + 1; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;
+        uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
+        for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(size_t)w2 * NT] = S.bits[wid][w2][lane];
+      } else {
+        // ---- tail: warps pull the remaining pixels; a warp composites 32 of
+        //      a pixel's entries per step with a prefix product of (1 - alpha)
+        if (!done) {
+          const int k = atomicAdd(&S.nact, 1);
+          S.apix[k] = (uint16_t)threadIdx.x;
+          S.st[threadIdx.x] = FwdState{T, C0, C1, C2, D, N0, N1, N2, last, 0u};
+        }
+        for (int w2 = 0; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;  // blended entries, set below
+        __syncthreads();
+        for (;;) {
+          int k = 0;
+          if (lane == 0) k = atomicAdd(&S.next, 1);
+          k = __shfl_sync(0xffffffffu, k, 0);
+          if (k >= n_act) break;
+          const int pth = S.apix[k];
+          const int pw = pth >> 5, pl = pth & 31;
+          const int qx = tx0 + (pw % WX) * 8 + (pl & 7), qy = ty0 + (pw / WX) * 4 + (pl >> 3);
+          const float fx = (float)qx + 0.5f, fy = (float)qy + 0.5f;
+          FwdState st = S.st[pth];
+          float acc[8] = {st.C0, st.C1, st.C2, st.D, st.N0, st.N1, st.N2, 0.f};
+          float tt = st.T;
+          uint32_t lst = st.last;
+          bool dn = false;
+          // this pixel's entries of the chunk, ascending
+          int nrel = 0;
+          for (int wd = 0; wd < (count + 31) >> 5; wd++) {
+            const int j = wd * 32 + lane;
+            const bool rel = j < count && in_tile_rect(__float_as_uint(S.rec.n[j].w), qx - tx0, qy - ty0);
+            const uint32_t bb = __ballot_sync(0xffffffffu, rel);
+            if (rel) S.list[wid][nrel + __popc(bb & lt_mask)] = (uint16_t)j;
+            nrel += __popc(bb);
+          }
+          __syncwarp();
+          for (int g = 0; g < nrel && !dn; g += 32) {
+            const bool has = g + lane < nrel;
+            const int j = has ? (int)S.list[wid][g + lane] : 0;
+            Pair e;
+            float alpha = 0.f;
+            if (has) {
+              eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], fx, fy, P.lp_scale, P.alpha_max, e);
+              alpha = e.alpha;
+            }
+            const bool kept = has && alpha >= P.alpha_min;
+            const float f = kept ? __fsub_rn(1.f, alpha) : 1.f;
+            const float Pin = warp_scan_mul(f, lane);
+            float Pex = __shfl_up_sync(0xffffffffu, Pin, 1);
+            if (lane == 0) Pex = 1.f;
+            const float Tb = __fmul_rn(tt, Pex), Ta = __fmul_rn(tt, Pin);
+            const uint32_t stopb = __ballot_sync(0xffffffffu, kept && Ta < P.t_min);
+            const int sl = stopb ? __ffs(stopb) - 1 : 32;
+            const bool contrib = kept && lane < sl;
+            const float w = contrib ? __fmul_rn(alpha, Tb) : 0.f;
+            float vals[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (contrib) {
+              const float4 col = S.rec.col[j], nrm = S.rec.n[j];
+              vals[0] = w * col.x; vals[1] = w * col.y; vals[2] = w * col.z;
+              vals[3] = w * pair_depth(e, col.w, S.rec.q[j].z, P.depth_ray);
+              vals[4] = w * nrm.x; vals[5] = w * nrm.y; vals[6] = w * nrm.z;
+            }
+            warp_sum8_all(vals, lane);
 #pragma unroll
-      for (int wd = 0; wd < NWD; wd++)
-        if (wd < nwd && bm_ok) bm[(int64_t)wd * NT] = blw[wd];
+            for (int q = 0; q < 7; q++) acc[q] += vals[q];
+            n_eval += (has && lane <= sl) ? 1u : 0u;
+            n_blend += contrib ? 1u : 0u;
+            if (contrib) atomicOr(&S.bits[pw][j >> 5][pl], 1u << (j & 31));
+            const uint32_t cb = __ballot_sync(0xffffffffu, contrib);
+            if (cb) lst = (uint32_t)(base + __shfl_sync(0xffffffffu, j, 31 - __clz(cb)) + 1);
+            if (stopb) {
+              tt = __shfl_sync(0xffffffffu, Tb, sl);
+              dn = true;
+            } else {
+              tt = __shfl_sync(0xffffffffu, Ta, 31);
+            }
+          }
+          if (lane == 0)
+            S.st[pth] = FwdState{tt, acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6], lst, dn ? 1u : 0u};
+          __syncwarp();
+        }
+        __syncthreads();
+        uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
+        for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(size_t)w2 * NT] = S.bits[wid][w2][lane];
+        if (!done) {
+          const FwdState st = S.st[threadIdx.x];
+          T = st.T; C0 = st.C0; C1 = st.C1; C2 = st.C2; D = st.D;
+          N0 = st.N0; N1 = st.N1; N2 = st.N2;
+          last = st.last;
+          done = st.done != 0u;
+        }
+      }
     }
     if (inside) {
       const int64_t HW = (int64_t)vw.W * vw.H;
@@ -914,37 +976,27 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
 // non-negative floats (ordered like the values), first per tile in shared
 // memory, then once per (tile, surfel) with a global atomicMax.
 // ---------------------------------------------------------------------------
-template <int CHUNK>
-struct ErrSmem {
-  SRecs<CHUNK> rec;
-  uint32_t emax[CHUNK];  // per entry of the chunk: largest error bits of a pixel that blends it
-  int item;
-  uint32_t top;
-};
-
-template <int TW, int TH, int CHUNK>
+template <int TW, int TH>
 __global__ void __launch_bounds__(TW* TH) k_max_error(const RenderArgs A, const float* __restrict__ err,
                                                       uint32_t* __restrict__ max_err) {
-  constexpr int NT = TW * TH, WX = TW / 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ErrSmem<CHUNK>& S = *reinterpret_cast<ErrSmem<CHUNK>*>(smem_raw);
+  constexpr int NT = TW * TH, WX = TW / 8, MCH = 256;  // entries per pass
+  __shared__ uint32_t emax[MCH];  // per entry of the pass: largest error bits of a pixel that blends it
+  __shared__ int s_item;
+  __shared__ uint32_t s_top;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const RastParams& P = A.P;
   if (A.hdr->status != 0) return;
   for (;;) {
-    if (threadIdx.x == 0) S.item = (int)atomicAdd(&A.hdr->queue_aux, 1u);
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&A.hdr->queue_aux, 1u);
     __syncthreads();
-    const int item = S.item;
+    const int item = s_item;
     if (item >= A.T) break;
     const int t = (int)__ldg(A.order + item);
     const int v = find_view_by_tile(A.views, A.V, t);
     const DView& vw = A.views[v];
     const int lt = t - vw.tile_base;
     const int tx0 = (lt % vw.tiles_x) * TW, ty0 = (lt / vw.tiles_x) * TH;
-    const int bx = tx0 + (wid % WX) * 8, by = ty0 + (wid / WX) * 4;
-    const int ipx = bx + (lane & 7), ipy = by + (lane >> 3);
+    const int ipx = tx0 + (wid % WX) * 8 + (lane & 7), ipy = ty0 + (wid / WX) * 4 + (lane >> 3);
     const bool inside = ipx < vw.W && ipy < vw.H;
-    const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
     uint32_t my_last = range.x, ebits = 0u;
     if (inside) {
@@ -953,37 +1005,34 @@ __global__ void __launch_bounds__(TW* TH) k_max_error(const RenderArgs A, const 
       ebits = e > 0.f ? __float_as_uint(e) : 0u;  // negative and NaN errors count as zero
       if (ebits) my_last = A.last[pix];
     }
-    if (threadIdx.x == 0) S.top = range.x;
+    if (threadIdx.x == 0) s_top = range.x;
     __syncthreads();
-    if (my_last > range.x) atomicMax(&S.top, my_last);
+    if (my_last > range.x) atomicMax(&s_top, my_last);
     __syncthreads();
-    const uint32_t top = S.top;
-    __syncthreads();
-    for (int64_t lo = range.x; lo < (int64_t)top; lo += CHUNK) {
-      const int count = (int)min64(CHUNK, (int64_t)top - lo);
+    const uint32_t top = s_top;
+    const int64_t woff = (int64_t)(range.x >> 5) + t;
+    for (int64_t lo = range.x; lo < (int64_t)top; lo += MCH) {
+      const int count = (int)min64(MCH, (int64_t)top - lo);
       const int nwd = (count + 31) >> 5;
-      stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, nullptr, lo + CHUNK,
-                             (int)max64(min64(CHUNK, (int64_t)top - lo - CHUNK), 0));
-      for (int j = threadIdx.x; j < count; j += NT) S.emax[j] = 0u;
+      for (int j = threadIdx.x; j < count; j += NT) emax[j] = 0u;
       __syncthreads();
-      const int lim = (int)min64(max64((int64_t)my_last - lo, 0), count);
-      for (int wd = 0; wd < nwd; wd++) {
-        uint32_t b = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
-        const int keep = lim - wd * 32;
-        b = keep >= 32 ? b : (keep <= 0 ? 0u : (b & ((1u << keep) - 1u)));
-        while (b) {
-          const int j = wd * 32 + __ffs(b) - 1;
-          b &= b - 1;
-          Pair e;
-          eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], px, py, P.lp_scale, P.alpha_max, e);
-          if (e.alpha >= P.alpha_min) atomicMax(&S.emax[j], ebits);
+      const int64_t w0 = woff + ((lo - (int64_t)range.x) >> 5);
+      if (ebits && s2d_check(w0 + nwd <= A.bmask_words, A.hdr)) {
+        for (int wd = 0; wd < nwd; wd++) {
+          uint32_t m = __ldg(A.bmask + (w0 + wd) * NT + threadIdx.x);
+          while (m) {
+            const int j = wd * 32 + __ffs(m) - 1;
+            m &= m - 1;
+            atomicMax(&emax[j], ebits);
+          }
         }
       }
       __syncthreads();
       for (int j = threadIdx.x; j < count; j += NT) {
-        const uint32_t m = S.emax[j];
+        const uint32_t m = emax[j];
+        if (!m) continue;
         const uint32_t sj = __ldg(A.vals + lo + j);
-        if (m && s2d_check((int64_t)sj >= vw.soff && (int64_t)sj < vw.soff + vw.scnt, A.hdr)) atomicMax(max_err + sj, m);
+        if (s2d_check((int64_t)sj >= vw.soff && (int64_t)sj < vw.soff + vw.scnt, A.hdr)) atomicMax(max_err + sj, m);
       }
       __syncthreads();
     }
@@ -1056,18 +1105,16 @@ static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int TW, int TH, int CHUNK>
+template <int TW, int TH>
 static cudaError_t run_max_error(const RenderArgs& A, const float* err, uint32_t* max_err, cudaStream_t st) {
-  auto k = k_max_error<TW, TH, CHUNK>;
-  constexpr size_t smem = sizeof(ErrSmem<CHUNK>);
+  auto k = k_max_error<TW, TH>;
   static int grid = -1;
   static int64_t grid_T = -1;
-  if (grid < 0) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (grid < 0 || grid_T != A.T) {
-    grid = persistent_grid(k, TW * TH, smem, A.T);
+    grid = persistent_grid(k, TW * TH, 0, A.T);
     grid_T = A.T;
   }
-  k<<<grid, TW * TH, smem, st>>>(A, err, max_err);
+  k<<<grid, TW * TH, 0, st>>>(A, err, max_err);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -1129,7 +1176,10 @@ cudaError_t launch_max_error(const Layout& L, const RastParams& P, int chunk, ch
   cudaError_t e = cudaMemsetAsync(&hdr->queue_aux, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   uint32_t* m = reinterpret_cast<uint32_t*>(max_err);
-  S2D_DISPATCH(run_max_error, P.tile_w, P.tile_h, chunk, A, err, m, st);
+  if (P.tile_w == 8 && P.tile_h == 8) return run_max_error<8, 8>(A, err, m, st);
+  if (P.tile_w == 16 && P.tile_h == 16) return run_max_error<16, 16>(A, err, m, st);
+  if (P.tile_w == 32 && P.tile_h == 8) return run_max_error<32, 8>(A, err, m, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace s2d

@@ -6,10 +6,12 @@ decisions the oracle flags as within rounding against either outcome of
 those decisions), and the gradients of an upstream gradient that is nonzero
 only at the sampled pixels of one view (so the oracle's sampled reverse pass
 is the whole gradient)."""
+import numpy as np
 import pytest
 import torch
 
-from gpu_utils import GRAD_REL_L2, MAX_UNRESOLVED, sampled_backward, sampled_forward, to_dev
+import oracle
+from gpu_utils import GRAD_REL_L2, MAX_UNRESOLVED, rel_l2, sampled_backward, sampled_forward, to_dev
 from paper_2604_03092_gb300 import autotune, scenes
 from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer
 
@@ -53,3 +55,86 @@ def test_backward_sampled_pixels_full_size(submap):
     print(out)
     for k, e in out.items():
         assert e <= GRAD_REL_L2, (k, out)
+
+
+def _crop_loss(sc, cand, s_local, name, comp, value, view, win, g8w):
+    """L = sum(g8w * outputs) over the pixel window `win` (x0, y0, x1, y1) of
+    `view`, rendered by the oracle in definition mode (every candidate surfel
+    at every pixel of the window: Eq. 1 as stated) from the candidate surfels
+    `cand` (ascending global indices, so ties keep their order), with
+    parameter `name`[comp] of candidate s_local set to `value`; also returns
+    the decision signature of every pixel."""
+    import copy
+    arrs = {k: np.ascontiguousarray(getattr(sc, k)[cand]) for k in ("means", "scales", "quats", "opacity", "rgb")}
+    a = arrs[name].reshape(len(cand), -1)
+    a[s_local, comp] = np.float32(value)
+    x0, y0, x1, y1 = win
+    v = copy.copy(view)
+    v.width, v.height = x1 - x0 + 1, y1 - y0 + 1
+    v.cx, v.cy = view.cx - x0, view.cy - y0
+    p = oracle.preprocess(arrs["means"], arrs["scales"], arrs["quats"], arrs["opacity"], arrs["rgb"], v,
+                          oracle.Config())
+    im = oracle.render(p, 0)
+    return float((im.out * g8w).sum()), im.phash, float(a[s_local, comp])
+
+
+def test_gradients_match_central_differences_full_size(submap):
+    """The refinement's gradient at the full benchmark size, spot-checked on
+    64 random parameters against FP64 central differences of the oracle: the
+    upstream gradient is that of the L1 RGB + 0.1 L1 depth loss against the
+    keyframe's ray-cast target, on one view; a surfel changes only the pixels
+    of its footprint there, so each difference renders that window (from the
+    surfels that reach it).  Parameters whose step flips a discrete decision
+    are redrawn."""
+    sc, cfg, params, rast, im = submap
+    v = 11
+    view = sc.views[v]
+    H, W = view.height, view.width
+    img = rast.view_images(im, v)
+    out8 = torch.cat([img.rgb, img.depth[None], img.normal, img.alpha[None]]).cpu().numpy().astype(np.float64)
+    g8 = np.zeros((8, H, W))
+    g8[0:3] = np.sign(out8[0:3] - sc.target_rgb[v]) / (3 * H * W)
+    g8[3] = 0.1 * np.sign(out8[3] - sc.target_depth[v]) / (H * W)
+    P = rast.n_pixels
+    o = int(rast._cviews[v].pixel_offset)
+    d = [np.zeros(3 * P, np.float32), np.zeros(P, np.float32), None, None]
+    d[0][3 * o:3 * o + 3 * H * W] = g8[0:3].reshape(-1)
+    d[1][o:o + H * W] = g8[3].reshape(-1)
+    grads = rast.backward(*params, [None if x is None else torch.from_numpy(x).cuda() for x in d])
+    gpu = {k: getattr(grads, k).cpu().numpy().astype(np.float64).reshape(sc.n, -1)
+           for k in ("means", "scales", "quats", "opacity", "rgb")}
+    p = oracle.preprocess_scene_view(sc, v, oracle.Config(tile_w=cfg.tile_w, tile_h=cfg.tile_h))
+    rect = p.amb[:, 0:4]  # widest pixel rect: every pixel a surfel may reach
+    vis = np.flatnonzero((p.status == oracle.ST_VISIBLE) & (np.abs(gpu["opacity"][:, 0]) > 0))
+    rng = np.random.default_rng(2024)
+    comps = {"means": 3, "scales": 2, "quats": 4, "opacity": 1, "rgb": 3}
+    names = list(comps)
+    fd_all, an_all = [], []
+    tries = 0
+    while len(fd_all) < 64 and tries < 200:
+        tries += 1
+        s = int(rng.choice(vis))
+        name = names[tries % len(names)]
+        comp = int(rng.integers(comps[name]))
+        win = (max(rect[s, 0], 0), max(rect[s, 1], 0), min(rect[s, 2], W - 1), min(rect[s, 3], H - 1))
+        reach = (rect[:, 0] <= win[2]) & (rect[:, 2] >= win[0]) & (rect[:, 1] <= win[3]) & (rect[:, 3] >= win[1])
+        reach &= (p.status == oracle.ST_VISIBLE) | (p.sflags != 0)
+        cand = np.flatnonzero(reach)
+        s_local = int(np.searchsorted(cand, s))
+        g8w = g8[:, win[1]:win[3] + 1, win[0]:win[2] + 1]
+        v0 = float(getattr(sc, name).reshape(sc.n, -1)[s, comp])
+        # a step small against the surfel's own size for positions and scales
+        h = (1e-3 * float(sc.scales[s].min()) if name == "means" else
+             1e-3 * float(sc.scales[s, comp]) if name == "scales" else 1e-4)
+        Lp, hp, vp = _crop_loss(sc, cand, s_local, name, comp, v0 + h, view, win, g8w)
+        Lm, hm, vm = _crop_loss(sc, cand, s_local, name, comp, v0 - h, view, win, g8w)
+        if not np.array_equal(hp, hm) or vp == vm:
+            continue
+        fd_all.append((Lp - Lm) / (vp - vm))
+        an_all.append(gpu[name][s, comp])
+    fd, an = np.array(fd_all), np.array(an_all)
+    print(f"{len(fd)} parameters checked in {tries} draws; rel L2 {rel_l2(an, fd):.2e}")
+    assert len(fd) == 64
+    assert rel_l2(an, fd) <= GRAD_REL_L2
+    scale = np.sqrt(np.mean(fd ** 2))
+    assert np.all(np.abs(an - fd) <= 5e-3 * np.abs(fd) + 1e-3 * scale), np.max(np.abs(an - fd) / (np.abs(fd) + scale))
