@@ -533,6 +533,7 @@ def main():
     # ---- per-view plain launches (classic pattern: one view per launch
     #      sequence, a host sync per view to size the sort) -------------------
     plain_vps = None
+    plain_stages = None
     if args.plain_steps > 0 and rank == 0:
         # one single-view rasterizer per distinct (image size, intrinsics,
         # surfel range), built before timing; each view re-uses its group's
@@ -569,6 +570,43 @@ def main():
                     nviews += 1
         torch.cuda.synchronize()
         plain_vps = nviews / (time.perf_counter() - t0)
+        # where the per-view path spends its time: one more pass with CUDA
+        # events around each of its stages (the status read is the host
+        # synchronisation the per-view path needs to size its sort), and the
+        # host wall time of the whole pass
+        names = ["preprocess", "bin_sort", "render_fwd", "status_sync", "render_bwd", "preprocess_bwd"]
+        acc = {n: 0.0 for n in names}
+        t0 = time.perf_counter()
+        nv = 0
+        for key, vs in groups.items():
+            one, one_out, one_grads = singles[key]
+            for v in vs:
+                one.set_view_pose(0, sc.views[v].Rt)
+                o = int(rast._cviews[v].pixel_offset)
+                H, W = rast.sizes[v]
+                dv = (d_rgb[3 * o:3 * o + 3 * H * W], d_depth[o:o + H * W], None, None)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+                ev[0].record()
+                one.preprocess(*params)
+                ev[1].record()
+                one.bin_sort()
+                ev[2].record()
+                one.render_fwd(one_out)
+                ev[3].record()
+                if one.status() != 0:
+                    raise SystemExit("device status in the per-view pass")
+                ev[4].record()
+                one.render_bwd_tiles(dv)
+                ev[5].record()
+                one.preprocess_bwd(*params, one_grads)
+                ev[6].record()
+                torch.cuda.synchronize()
+                for i, n in enumerate(names):
+                    acc[n] += ev[i].elapsed_time(ev[i + 1])
+                nv += 1
+        wall = (time.perf_counter() - t0) * 1e3 / nv
+        plain_stages = {n: acc[n] / nv for n in names}
+        plain_stages["host_wall_per_view"] = wall
         del singles
 
     # ---- end to end through the public API with host buffers -----------------
@@ -715,6 +753,8 @@ def main():
             "stages_ms": stage_ms, "stage_roofline": stage_frac, "composite_roofline_frac": composite,
             "roofline": roof, "clocks": clocks,
             "graph_views_per_s": graph_vps, "plain_per_view_views_per_s": plain_vps,
+            "plain_per_view_stages_ms": plain_stages,
+            "batched_stages_ms_per_view": {k: v / V for k, v in stage_ms.items()},
             "e2e": {"value": e2e_vps, "unit": "views/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "pairs": {k: st[k] for k in ("fwd_pairs_evaluated", "fwd_pairs_blended", "bwd_pairs_evaluated",
