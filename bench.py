@@ -378,6 +378,8 @@ def main():
     ap.add_argument("--chunk", type=int, default=None)
     ap.add_argument("--fwd-tail", type=int, default=None, help="forward tail threshold per warp (255 = always)")
     ap.add_argument("--bwd-chunk", type=int, default=None, help="chunk of the backward pass (default: --chunk)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time every launch-shape candidate on this workload first (autotune.tune), then use the best")
     ap.add_argument("--plain-steps", type=int, default=2, help="steps of the per-view plain-launch baseline (0=skip)")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--refine-iters", type=int, default=100,
@@ -415,6 +417,14 @@ def main():
               (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
 
     cfg = RasterConfig(stats=True)
+    tune_ms = None
+    if args.autotune:
+        gen = torch.Generator(device=dev).manual_seed(0)
+        P = sum(v.width * v.height for v in sc.views)
+        d_tune = (torch.randn(3 * P, device=dev, generator=gen) * 1e-6, torch.randn(P, device=dev, generator=gen) * 1e-7,
+                  None, None)
+        best, tune_ms = autotune.tune(sc.views, sc.n, autotune.cuda_runner(sc.views, params, d_tune), force=True)
+        torch.cuda.empty_cache()
     tuned = autotune.lookup(sc.views, sc.n) if args.tile is None else None
     if tuned:
         cfg.tile_w, cfg.tile_h, cfg.chunk, cfg.bwd_chunk = tuned
@@ -761,6 +771,7 @@ def main():
                                          "bwd_pairs_blended", "bwd_terms_outside")},
             "cpu_baseline": cpu,
             "refinement": refine,
+            "autotune_ms": tune_ms,
             "map_maintenance": maint,
         }
         print(json.dumps(line), flush=True)

@@ -173,8 +173,10 @@ void splat2d_default_config(splat2d_config* cfg);
 
 /* Bytes of workspace the problem needs (0 if the arguments are invalid).
  * The workspace holds, per (view, surfel) pair of every view's range, an
- * 80-byte render record, an 80-byte gradient record and a 4-byte tile count,
- * plus 24 bytes per unit of instance_capacity and 8 bytes per pixel. */
+ * 80-byte render record, an 80-byte gradient record and a 4-byte tile count;
+ * per unit of instance_capacity, 24 bytes of sort keys and values, an 80-byte
+ * sorted-order record copy and tile_w * tile_h / 8 bytes of blended-pair
+ * masks; and 12 bytes per pixel. */
 size_t splat2d_workspace_size(const splat2d_config* cfg, const splat2d_problem* prob);
 
 /*
@@ -266,6 +268,38 @@ int splat2d_render_bwd_tiles(const splat2d_config* cfg, const splat2d_problem* p
                              splat2d_stream stream);
 int splat2d_preprocess_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
                            void* ws, size_t ws_bytes, const splat2d_grads* grads, splat2d_stream stream);
+
+/*
+ * Follows: the 2D Gaussian surfel primitive the paper adopts (Sec. 3) comes
+ * with a depth-distortion regulariser: per pixel, over the surfels it blends
+ * in blending order,
+ *     D_s = 2 sum_i sum_{j<i} w_i w_j (z_i - z_j),
+ * z the depth each surfel contributes to the depth output (the center's z_i,
+ * or with SPLAT2D_FLAG_DEPTH_RAY the ray-splat intersection depth).  With the
+ * center depth -- the sort key, non-decreasing along the blending order --
+ * this is sum_{i,j} w_i w_j |z_i - z_j|; with the ray depth it is the same
+ * ordered sum (the intersection depths need not be sorted).
+ *
+ * splat2d_render_fwd_dist is splat2d_render_fwd that also writes D_s to
+ * `dist` (device, one float per packed pixel, laid out like `alpha`; NULL
+ * gives exactly splat2d_render_fwd).  splat2d_render_bwd_dist and
+ * splat2d_render_bwd_tiles_dist are splat2d_render_bwd and
+ * splat2d_render_bwd_tiles that also take d_dist, the upstream gradient of
+ * D_s (same layout; NULL = zero), and add its gradient -- through the
+ * weights and the depths -- to every parameter and pose gradient.  They
+ * must follow a forward on the same workspace (either forward keeps what the
+ * distortion's adjoint needs).  Errors as for the calls they extend.
+ */
+int splat2d_render_fwd_dist(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                            float* rgb, float* depth, float* normal, float* alpha, float* dist,
+                            splat2d_stream stream);
+int splat2d_render_bwd_dist(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                            void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth,
+                            const float* d_normal, const float* d_alpha, const float* d_dist,
+                            const splat2d_grads* grads, splat2d_stream stream);
+int splat2d_render_bwd_tiles_dist(const splat2d_config* cfg, const splat2d_problem* prob, void* ws,
+                                  size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
+                                  const float* d_alpha, const float* d_dist, splat2d_stream stream);
 
 /*
  * Map fusion, pruning input (Sec. 4.3, "Map Fusion": the global map is

@@ -66,7 +66,8 @@ def _load():
         lib.oracle_preprocess.argtypes = [i64] + [P] * 7 + [P] * 7
         lib.oracle_render.argtypes = [ctypes.c_int, i64] + [P] * 8 + [P] * 5
         lib.oracle_render_pixels.argtypes = [ctypes.c_int, i64] + [P] * 8 + [i64, P] + [P] * 4
-        lib.oracle_render_bwd.argtypes = [ctypes.c_int, i64] + [P] * 9 + [i64, P, P]
+        lib.oracle_render_bwd.argtypes = [ctypes.c_int, i64] + [P] * 9 + [i64, P, P, P]
+        lib.oracle_render_dist.argtypes = [ctypes.c_int, i64] + [P] * 8 + [P]
         lib.oracle_chain.argtypes = [i64] + [P] * 12
         lib.oracle_render_pixels_variants.argtypes = ([ctypes.c_int, i64] + [P] * 8
                                                       + [ctypes.c_int, ctypes.c_int, i64, P, P])
@@ -242,23 +243,37 @@ class Grads:
     pose: np.ndarray  # (6,) d rho, d phi
 
 
+def render_dist(prep: Prep, mode: int = 1) -> np.ndarray:
+    """Depth distortion per pixel (H, W): 2 sum_i sum_{j<i} w_i w_j (z_i - z_j)
+    over the pixel's blended entries in blending order."""
+    lib = _load()
+    W, H = int(prep.cam[0]), int(prep.cam[1])
+    out = np.zeros((H, W))
+    lib.oracle_render_dist(mode, prep.rec.shape[0], _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb),
+                           _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(out))
+    return out
+
+
 def render_bwd(means, scales, quats, prep: Prep, g8: np.ndarray, mode: int = 1,
-               pix: Optional[np.ndarray] = None, grads: Optional[Grads] = None) -> Grads:
-    """Gradients of sum(g8 * outputs) for one view; accumulated into `grads`."""
+               pix: Optional[np.ndarray] = None, grads: Optional[Grads] = None,
+               g_dist: Optional[np.ndarray] = None) -> Grads:
+    """Gradients of sum(g8 * outputs) (+ sum(g_dist * distortion)) for one
+    view; accumulated into `grads`."""
     lib = _load()
     means, scales, quats = _c(means, np.float32), _c(scales, np.float32), _c(quats, np.float32)
     n = prep.rec.shape[0]
     g8 = _c(g8, np.float64)
+    gd = None if g_dist is None else _c(g_dist, np.float64)
     grec = np.zeros((n, NREC))
     if pix is None:
         lib.oracle_render_bwd(mode, n, _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb),
                               _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(g8), -1, None,
-                              _p(grec))
+                              _p(grec), None if gd is None else _p(gd))
     else:
         pix = _c(pix, np.int64)
         lib.oracle_render_bwd(mode, n, _p(prep.rec), _p(prep.status), _p(prep.pixrect), _p(prep.amb),
                               _p(prep.zbits), _p(prep.sflags), _p(prep.cam), _p(prep.cfg), _p(g8),
-                              pix.shape[0], _p(pix), _p(grec))
+                              pix.shape[0], _p(pix), _p(grec), None if gd is None else _p(gd))
     if grads is None:
         grads = Grads(np.zeros((n, 3)), np.zeros((n, 2)), np.zeros((n, 4)), np.zeros(n), np.zeros((n, 3)),
                       np.zeros(6))

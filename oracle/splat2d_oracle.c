@@ -683,16 +683,64 @@ int oracle_max_error(int mode, int64_t n, const double* rec, const int32_t* stat
 }
 
 /*
+ * Depth distortion of one view (the regulariser of the 2DGS surfel the paper
+ * adopts, Sec. 3): per pixel, over its blended entries in blending order,
+ *     D = 2 sum_i sum_{j<i} w_i w_j (z_i - z_j),
+ * z the depth each entry contributes to the depth output.  When those
+ * depths do not decrease along the blending order -- always for the center
+ * depth, which is the sort key -- this is sum_{i,j} w_i w_j |z_i - z_j|.
+ * Written as the plain double sum.  out: [H][W].
+ */
+int oracle_render_dist(int mode, int64_t n, const double* rec, const int32_t* status, const int32_t* pixrect,
+                       const int32_t* amb, const uint32_t* zbits, const uint32_t* sflags, const double* camv,
+                       const double* cfgv, double* out) {
+  cam_t cam;
+  cfg_t cfg;
+  load_cam(camv, &cam);
+  load_cfg(cfgv, &cfg);
+  view_t V;
+  build_view(&V, mode, n, rec, status, pixrect, amb, zbits, sflags, &cam, &cfg);
+  int64_t P = (int64_t)cam.W * cam.H;
+#pragma omp parallel
+  {
+    int64_t cap = 4096;
+    blend_t* list = (blend_t*)malloc(sizeof(blend_t) * cap);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t p = 0; p < P; p++) {
+      int ix = (int)(p % cam.W), iy = (int)(p / cam.W);
+      int64_t nb = walk_pixel(&V, &cfg, ix, iy, NULL, NULL, NULL, NULL, list, cap);
+      if (nb > cap) {
+        cap = nb;
+        list = (blend_t*)realloc(list, sizeof(blend_t) * cap);
+        nb = walk_pixel(&V, &cfg, ix, iy, NULL, NULL, NULL, NULL, list, cap);
+      }
+      double d = 0;
+      for (int64_t i = 0; i < nb; i++)
+        for (int64_t j = 0; j < i; j++) {
+          double wi = list[i].e.alpha * list[i].T, wj = list[j].e.alpha * list[j].T;
+          d += 2.0 * wi * wj * (list[i].e.z - list[j].e.z);
+        }
+      out[p] = d;
+    }
+    free(list);
+  }
+  free_view(&V);
+  return 0;
+}
+
+/*
  * Reverse pass of one view.  Upstream gradients g8 are [8][H][W] (same
  * channel order as the outputs).  Record gradients (dL/d of the 19 record
  * fields) are accumulated into grec[n*20]; the chain rule to the surfel
  * parameters and the camera se(3) tangent is oracle_chain().  Only pixels
  * whose index is listed in pix (or all pixels if npix < 0) contribute.
+ * gdist ([H][W] or NULL) is the upstream gradient of the depth distortion
+ * (oracle_render_dist).
  */
 int oracle_render_bwd(int mode, int64_t n, const double* rec, const int32_t* status,
                       const int32_t* pixrect, const int32_t* amb, const uint32_t* zbits,
                       const uint32_t* sflags, const double* camv, const double* cfgv, const double* g8,
-                      int64_t npix, const int64_t* pix, double* grec) {
+                      int64_t npix, const int64_t* pix, double* grec, const double* gdist) {
   cam_t cam;
   cfg_t cfg;
   load_cam(camv, &cam);
@@ -724,6 +772,13 @@ int oracle_render_bwd(int mode, int64_t n, const double* rec, const int32_t* sta
       double px = ix + 0.5, py = iy + 0.5;
       /* suffix sums S_f = sum over later blended entries of w f, colour incl. T_final bg */
       double SC[3] = {tf * cfg.bg[0], tf * cfg.bg[1], tf * cfg.bg[2]}, SD = 0, SN[3] = {0, 0, 0};
+      /* depth distortion D = 2 sum_i w_i (z_i A_{i-1} - B_{i-1}), A_{i-1} and
+       * B_{i-1} the sums of w_j and w_j z_j in front of i.  Behind entry k:
+       * Asuf = sum w_i, Bsuf = sum w_i z_i, Wsuf = sum w_i dD/dw_i. */
+      const double gd = gdist ? gdist[p] : 0.0;
+      double Dtot = 0, Asuf = 0, Bsuf = 0, Wsuf = 0;
+      if (gd != 0)
+        for (int64_t k = 0; k < nb; k++) Dtot += list[k].e.alpha * list[k].T * list[k].e.z;
       for (int64_t k = nb - 1; k >= 0; k--) {
         const blend_t* b = &list[k];
         const double* r = rec + b->s * NREC;
@@ -736,14 +791,24 @@ int oracle_render_bwd(int mode, int64_t n, const double* rec, const int32_t* sta
           da += dC[c] * (Ti * r[R_RGB + c] - SC[c] / om);
         }
         const double zi = b->e.z;
+        double dzd = 0; /* dL/dz_k through the distortion */
+        if (gd != 0) {
+          const double Ap = 1.0 - Ti, Bp = Dtot - w * zi - Bsuf;  /* sums in front of k */
+          const double Wk = 2.0 * (zi * Ap - Bp + Bsuf - zi * Asuf);   /* dD/dw_k */
+          da += gd * (Wk * Ti - Wsuf / om);
+          dzd = gd * 2.0 * w * (Ap - Asuf);                            /* dD/dz_k */
+          Asuf += w;
+          Bsuf += w * zi;
+          Wsuf += Wk * w;
+        }
         if (b->e.zray) {
           /* z = det(M) / c with c = A[6] px + A[7] py + A[8] */
-          double dz = w * dD, c = b->e.c;
+          double dz = w * dD + dzd, c = b->e.c;
           g[R_DET] = dz / c;
           double x[3] = {px, py, 1.0};
           for (int j = 0; j < 3; j++) g[R_A + 6 + j] -= dz * zi / c * x[j];
         } else {
-          g[R_Z] = w * dD;
+          g[R_Z] = w * dD + dzd;
         }
         da += dD * (Ti * zi - SD / om);
         for (int c = 0; c < 3; c++) {

@@ -83,6 +83,14 @@ SIGNATURES = {
                                           ctypes.POINTER(Grads), c_void_p]),
     "splat2d_render_bwd_tiles": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem), c_void_p,
                                                 c_size_t, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "splat2d_render_fwd_dist": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem), c_void_p, c_size_t,
+                                               c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "splat2d_render_bwd_dist": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem),
+                                               ctypes.POINTER(Surfels), c_void_p, c_size_t, c_void_p, c_void_p,
+                                               c_void_p, c_void_p, c_void_p, ctypes.POINTER(Grads), c_void_p]),
+    "splat2d_render_bwd_tiles_dist": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem), c_void_p,
+                                                     c_size_t, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                                     c_void_p]),
     "splat2d_preprocess_bwd": (ctypes.c_int, [ctypes.POINTER(Config), ctypes.POINTER(Problem),
                                               ctypes.POINTER(Surfels), c_void_p, c_size_t, ctypes.POINTER(Grads),
                                               c_void_p]),

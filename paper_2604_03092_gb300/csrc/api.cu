@@ -165,6 +165,7 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->tile_class = take(sizeof(uint32_t) * 4 * (size_t)T);  // one list per bucket-sort size class
   L->tfinal = take(sizeof(float) * P);
   L->last = take(sizeof(uint32_t) * P);
+  L->dfinal = take(sizeof(float) * P);  // per pixel: the depth sum D (the depth-distortion adjoint needs it)
   // the records in sorted-list order, written by the forward as it stages
   // them and read back contiguously by the backward
   L->rcopy = take(sizeof(float4) * REC_F4 * (size_t)L->cap);
@@ -295,15 +296,37 @@ int splat2d_bin_sort(const splat2d_config* cfg, const splat2d_problem* prob, voi
   return SPLAT2D_OK;
 }
 
-int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
-                       float* rgb, float* depth, float* normal, float* alpha, splat2d_stream stream) {
+int splat2d_render_fwd_dist(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                            float* rgb, float* depth, float* normal, float* alpha, float* dist,
+                            splat2d_stream stream) {
   Layout L;
   int rc = check_common(cfg, prob, ws, ws_bytes, &L);
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(ws);
   const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
-  if (launch_render_fwd(L, make_params(cfg), cfg->chunk, w, vals, rgb, depth, normal, alpha, st) != cudaSuccess)
+  if (launch_render_fwd(L, make_params(cfg), cfg->chunk, w, vals, rgb, depth, normal, alpha, dist, st) !=
+      cudaSuccess)
+    return SPLAT2D_ERR_CUDA;
+  return SPLAT2D_OK;
+}
+
+int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
+                       float* rgb, float* depth, float* normal, float* alpha, splat2d_stream stream) {
+  return splat2d_render_fwd_dist(cfg, prob, ws, ws_bytes, rgb, depth, normal, alpha, nullptr, stream);
+}
+
+int splat2d_render_bwd_tiles_dist(const splat2d_config* cfg, const splat2d_problem* prob, void* ws,
+                                  size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
+                                  const float* d_alpha, const float* d_dist, splat2d_stream stream) {
+  Layout L;
+  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
+  if (rc) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(ws);
+  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
+  if (launch_render_bwd(L, make_params(cfg), cfg->bwd_chunk ? cfg->bwd_chunk : cfg->chunk, w, vals, d_rgb,
+                        d_depth, d_normal, d_alpha, d_dist, st) != cudaSuccess)
     return SPLAT2D_ERR_CUDA;
   return SPLAT2D_OK;
 }
@@ -311,16 +334,8 @@ int splat2d_render_fwd(const splat2d_config* cfg, const splat2d_problem* prob, v
 int splat2d_render_bwd_tiles(const splat2d_config* cfg, const splat2d_problem* prob, void* ws, size_t ws_bytes,
                              const float* d_rgb, const float* d_depth, const float* d_normal, const float* d_alpha,
                              splat2d_stream stream) {
-  Layout L;
-  int rc = check_common(cfg, prob, ws, ws_bytes, &L);
-  if (rc) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  char* w = static_cast<char*>(ws);
-  const uint32_t* vals = reinterpret_cast<const uint32_t*>(w + (final_sorted_buffer(L) ? L.vals1 : L.vals0));
-  if (launch_render_bwd(L, make_params(cfg), cfg->bwd_chunk ? cfg->bwd_chunk : cfg->chunk, w, vals, d_rgb, d_depth, d_normal, d_alpha, st) !=
-      cudaSuccess)
-    return SPLAT2D_ERR_CUDA;
-  return SPLAT2D_OK;
+  return splat2d_render_bwd_tiles_dist(cfg, prob, ws, ws_bytes, d_rgb, d_depth, d_normal, d_alpha, nullptr,
+                                       stream);
 }
 
 int splat2d_preprocess_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
@@ -395,13 +410,21 @@ int splat2d_sim3_apply(int64_t n, float* means, float* quats, float* scales, con
   return SPLAT2D_OK;
 }
 
+int splat2d_render_bwd_dist(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
+                            void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth,
+                            const float* d_normal, const float* d_alpha, const float* d_dist,
+                            const splat2d_grads* grads, splat2d_stream stream) {
+  if (!surfels || !prob || surfels->n != prob->n_surfels || !grads) return SPLAT2D_ERR_INVALID_ARG;
+  int rc = splat2d_render_bwd_tiles_dist(cfg, prob, ws, ws_bytes, d_rgb, d_depth, d_normal, d_alpha, d_dist, stream);
+  if (rc) return rc;
+  return splat2d_preprocess_bwd(cfg, prob, surfels, ws, ws_bytes, grads, stream);
+}
+
 int splat2d_render_bwd(const splat2d_config* cfg, const splat2d_problem* prob, const splat2d_surfels* surfels,
                        void* ws, size_t ws_bytes, const float* d_rgb, const float* d_depth, const float* d_normal,
                        const float* d_alpha, const splat2d_grads* grads, splat2d_stream stream) {
-  if (!surfels || !prob || surfels->n != prob->n_surfels || !grads) return SPLAT2D_ERR_INVALID_ARG;
-  int rc = splat2d_render_bwd_tiles(cfg, prob, ws, ws_bytes, d_rgb, d_depth, d_normal, d_alpha, stream);
-  if (rc) return rc;
-  return splat2d_preprocess_bwd(cfg, prob, surfels, ws, ws_bytes, grads, stream);
+  return splat2d_render_bwd_dist(cfg, prob, surfels, ws, ws_bytes, d_rgb, d_depth, d_normal, d_alpha, nullptr,
+                                 grads, stream);
 }
 
 uint64_t splat2d_launch_count(void) { return s2d::launch_counter().load(); }

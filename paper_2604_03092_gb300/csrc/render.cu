@@ -136,6 +136,9 @@ struct RenderArgs {
   float* alpha;
   float* tfinal;
   uint32_t* last;
+  float* dist;          // depth distortion output (forward; null: not asked for)
+  float* dfinal;        // per pixel depth sum D, kept for the distortion's adjoint
+  const float* d_dist;  // upstream gradient of the distortion (backward; null: none)
   const float* d_rgb;
   const float* d_depth;
   const float* d_normal;
@@ -299,7 +302,7 @@ __device__ __forceinline__ float warp_scan_add(float x, int lane) {
 
 // Per-pixel state of the forward while it is handed between warps.
 struct FwdState {
-  float T, C0, C1, C2, D, N0, N1, N2;
+  float T, C0, C1, C2, D, N0, N1, N2, Ds;
   uint32_t last, done;
 };
 
@@ -317,7 +320,10 @@ struct FwdSmem {
 // Tail mode of the forward: once at most P.fwd_tail pixels of a tile per
 // warp are still compositing, all warps share them, one pixel at a time.
 
-template <int TW, int TH, int CHUNK>
+// DIST: also the depth distortion 2 sum_i sum_{j<i} w_i w_j (z_i - z_j) (front to
+// back: each blended pair adds 2 w (z A - D) with A = 1 - T and D the depth
+// sum in front of it).
+template <int TW, int TH, int CHUNK, bool DIST>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 12) : 3) k_render_fwd(const RenderArgs A) {
   constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -344,7 +350,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     const bool inside = ipx < vw.W && ipy < vw.H;
     const float px = (float)ipx + 0.5f, py = (float)ipy + 0.5f;
     const uint2 range = __ldg(A.ranges + t);
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, Ds = 0.f;
     uint32_t last = range.x;
     bool done = !inside;
     for (int64_t base = range.x; base < range.y; base += CHUNK) {
@@ -401,6 +407,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           C2 = __fmaf_rn(w, col.z, C2);
           float zp = col.w;
           if (P.depth_ray) zp = pair_depth(e, col.w, S.rec.q[j].z, 1);
+          if constexpr (DIST) Ds = __fmaf_rn(2.f * w, __fmaf_rn(zp, __fsub_rn(1.f, T), -D), Ds);
           D = __fmaf_rn(w, zp, D);
           N0 = __fmaf_rn(w, nrm.x, N0);
           N1 = __fmaf_rn(w, nrm.y, N1);
@@ -420,7 +427,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         if (!done) {
           const int k = atomicAdd(&S.nact, 1);
           S.apix[k] = (uint16_t)threadIdx.x;
-          S.st[threadIdx.x] = FwdState{T, C0, C1, C2, D, N0, N1, N2, last, 0u};
+          S.st[threadIdx.x] = FwdState{T, C0, C1, C2, D, N0, N1, N2, Ds, last, 0u};
         }
         for (int w2 = 0; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;  // blended entries, set below
         __syncthreads();
@@ -434,7 +441,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           const int qx = tx0 + (pw % WX) * 8 + (pl & 7), qy = ty0 + (pw / WX) * 4 + (pl >> 3);
           const float fx = (float)qx + 0.5f, fy = (float)qy + 0.5f;
           FwdState st = S.st[pth];
-          float acc[8] = {st.C0, st.C1, st.C2, st.D, st.N0, st.N1, st.N2, 0.f};
+          float acc[8] = {st.C0, st.C1, st.C2, st.D, st.N0, st.N1, st.N2, st.Ds};
           float tt = st.T;
           uint32_t lst = st.last;
           bool dn = false;
@@ -468,15 +475,23 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
             const bool contrib = kept && lane < sl;
             const float w = contrib ? __fmul_rn(alpha, Tb) : 0.f;
             float vals[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float zpair = 0.f;
             if (contrib) {
               const float4 col = S.rec.col[j], nrm = S.rec.n[j];
+              zpair = pair_depth(e, col.w, S.rec.q[j].z, P.depth_ray);
               vals[0] = w * col.x; vals[1] = w * col.y; vals[2] = w * col.z;
-              vals[3] = w * pair_depth(e, col.w, S.rec.q[j].z, P.depth_ray);
+              vals[3] = w * zpair;
               vals[4] = w * nrm.x; vals[5] = w * nrm.y; vals[6] = w * nrm.z;
+            }
+            if constexpr (DIST) {
+              // depth sum in front of each pair: the pixel's so far, then the group's own terms before it
+              const float wz = vals[3];
+              const float Bb = acc[3] + (warp_scan_add(wz, lane) - wz);
+              vals[7] = contrib ? 2.f * w * (zpair * (1.f - Tb) - Bb) : 0.f;
             }
             warp_sum8_all(vals, lane);
 #pragma unroll
-            for (int q = 0; q < 7; q++) acc[q] += vals[q];
+            for (int q = 0; q < 8; q++) acc[q] += vals[q];
             n_eval += (has && lane <= sl) ? 1u : 0u;
             n_blend += contrib ? 1u : 0u;
             if (contrib) atomicOr(&S.bits[pw][j >> 5][pl], 1u << (j & 31));
@@ -490,7 +505,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
             }
           }
           if (lane == 0)
-            S.st[pth] = FwdState{tt, acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6], lst, dn ? 1u : 0u};
+            S.st[pth] = FwdState{tt, acc[0], acc[1], acc[2], acc[3], acc[4], acc[5], acc[6], acc[7], lst, dn ? 1u : 0u};
           __syncwarp();
         }
         __syncthreads();
@@ -499,7 +514,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         if (!done) {
           const FwdState st = S.st[threadIdx.x];
           T = st.T; C0 = st.C0; C1 = st.C1; C2 = st.C2; D = st.D;
-          N0 = st.N0; N1 = st.N1; N2 = st.N2;
+          N0 = st.N0; N1 = st.N1; N2 = st.N2; Ds = st.Ds;
           last = st.last;
           done = st.done != 0u;
         }
@@ -522,8 +537,10 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         o[2 * HW] = N2;
       }
       if (A.alpha) A.alpha[vw.poff + pix] = 1.f - T;
+      if constexpr (DIST) A.dist[vw.poff + pix] = Ds;
       A.tfinal[vw.poff + pix] = T;
       A.last[vw.poff + pix] = last;
+      A.dfinal[vw.poff + pix] = D;
     }
   }
   if (P.stats) {
@@ -620,7 +637,7 @@ __device__ __forceinline__ void pair_grads_ray_depth(const Pair& e, const float4
 
 // Dynamic shared memory of the backward kernel (per-pixel arrays indexed by
 // the pixel's slot, see k_render_bwd).
-template <int NT, int CHUNK>
+template <int NT, int CHUNK, bool DIST>
 struct BwdSmem {
   SRecs<CHUNK> rec;
   float grad[CHUNK * SGRAD_STRIDE];
@@ -629,6 +646,10 @@ struct BwdSmem {
   uint16_t pcnt[NT][CHUNK / 32];   // per pixel: set bits in its mask words >= w (from the deepest word)
   float4 up[NT][2];                // per pixel: dC0 dC1 dC2 dD | dN0 dN1 dN2 dA*T_final
   float2 tq[NT];                   // per pixel: (T in front of the deepest unprocessed entry, Q behind it)
+  // depth distortion only: per pixel, the sums of w and w z over the entries
+  // behind the deepest unprocessed one, and (its upstream gradient, its depth sum D)
+  float2 ab[DIST ? NT : 1];
+  float2 gdz[DIST ? NT : 1];
   uint32_t gexp[(SGRAD_STRIDE + 1) / 2];  // per quantity, 16 bits: the upper half of this chunk's scale (+inf: none)
   float ginv[SGRAD_STRIDE];        // per quantity: inverse of the scale (0: none)
   uint32_t estat[SGRAD_STRIDE];    // per quantity: (sum of biased exponents of nonzero entry sums) << 10 | their number
@@ -638,6 +659,13 @@ struct BwdSmem {
   uint32_t top;
 };
 
+// DIST: also the adjoint of the depth distortion D_s = 2 sum_i w_i (z_i A_{i-1}
+// - B_{i-1}) (A, B the sums of w and w z in front of i): dD_s/dw_k = 2 (z_k
+// A_{k-1} - B_{k-1} + Bsuf_k - z_k Asuf_k) joins the pair's upstream feature
+// sum f (so the transmittance terms carry it to alpha), and dD_s/dz_k = 2 w_k
+// (A_{k-1} - Asuf_k) its depth gradient; Asuf, Bsuf (the sums behind k) are
+// two more segmented prefix sums along the pixel's run, B_{k-1} = D - w_k z_k
+// - Bsuf_k with D the pixel's depth sum kept by the forward.
 // The reverse pass streams (pixel, entry) pairs.  Per chunk, each warp
 // builds its 8x4 patch's per-pixel entry masks with ballots.  Then each warp
 // takes 32 pixels spread over the tile (a diagonal interleave, so the warps'
@@ -652,11 +680,11 @@ struct BwdSmem {
 // every lane adds its own pair's gradient terms to the entry's shared-memory
 // slot, and the last lane of each run stores the pixel's running (T, Q) for
 // its next run.
-template <int TW, int TH, int CHUNK>
+template <int TW, int TH, int CHUNK, bool DIST>
 __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 8) : 2) k_render_bwd(const RenderArgs A) {
   constexpr int NT = TW * TH, NW = NT / 32, WX = TW / 8, NWD = CHUNK / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BwdSmem<NT, CHUNK>& S = *reinterpret_cast<BwdSmem<NT, CHUNK>*>(smem_raw);
+  BwdSmem<NT, CHUNK, DIST>& S = *reinterpret_cast<BwdSmem<NT, CHUNK, DIST>*>(smem_raw);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t le_mask = (2u << lane) - 1u;  // lanes <= this lane
   const RastParams& P = A.P;
@@ -694,6 +722,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     const int64_t HW = (int64_t)vw.W * vw.H;
     uint32_t my_last = range.x;
     float T = 1.f, Q = 0.f;
+    float As = 0.f, Bs = 0.f;  // distortion: sums of w and w z behind the deepest unprocessed entry
     bool fixed = false;  // a tile's first chunk accumulates in float, every later one in fixed point
     bool restat = true;  // the scales are re-derived after every other chunk
     {
@@ -716,6 +745,10 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       }
       S.up[myslot][0] = u0;
       S.up[myslot][1] = u1;
+      if constexpr (DIST) {
+        const int64_t pix = (int64_t)ipy * vw.W + ipx;
+        S.gdz[myslot] = inside ? make_float2(A.d_dist[vw.poff + pix], A.dfinal[vw.poff + pix]) : make_float2(0.f, 0.f);
+      }
     }
     if (threadIdx.x == 0) S.top = range.x;
     if (threadIdx.x < (SGRAD_STRIDE + 1) / 2) S.gexp[threadIdx.x] = 0x7f807f80u;
@@ -765,6 +798,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         }
       }
       if (act) S.tq[myslot] = make_float2(T, Q);
+      if constexpr (DIST)
+        if (act) S.ab[myslot] = make_float2(As, Bs);
       __syncthreads();
       // this warp's stream: its pixels' pairs end to end
       const uint32_t cnt = S.pcnt[mine][0];
@@ -842,6 +877,28 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           const float4 nrm = S.rec.n[j];
           f = fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, fmaf(u1.z, nrm.z, f)));
         }
+        float dzd = 0.f, sa = 0.f, sb = 0.f;  // distortion: its depth gradient; the run's sums of w, w z
+        float2 ab = make_float2(0.f, 0.f);
+        if constexpr (DIST) {
+          // segmented prefix sums of w and w z: with the pixel's carried
+          // sums, those behind this pair
+          sa = w;
+          sb = w * zp;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float ya = __shfl_up_sync(0xffffffffu, sa, o);
+            const float yb = __shfl_up_sync(0xffffffffu, sb, o);
+            const bool in = lane - o >= s0;
+            sa = in ? sa + ya : sa;
+            sb = in ? sb + yb : sb;
+          }
+          ab = S.ab[ps];
+          const float2 gd = S.gdz[ps];
+          const float Asuf = ab.x + (sa - w), Bsuf = ab.y + (sb - w * zp);
+          const float Ap = 1.f - Tb, Bp = gd.y - w * zp - Bsuf;  // the sums in front of this pair
+          f = fmaf(gd.x * 2.f, zp * Ap - Bp + Bsuf - zp * Asuf, f);
+          dzd = gd.x * 2.f * w * (Ap - Asuf);
+        }
         const float wf = w * f;
         // segmented prefix sum: the sum over entries behind this one
         float sum = wf;
@@ -857,7 +914,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         float g[16];
         float gz;
         pair_grads(e, S.rec.p[j], qj, da, w, u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, P.lp_scale, g, gz);
-        if (P.depth_ray) pair_grads_ray_depth(e, qj, col.w, zp, w * u0.w, g, gz);
+        if constexpr (DIST) gz += dzd;
+        if (P.depth_ray) pair_grads_ray_depth(e, qj, col.w, zp, w * u0.w + dzd, g, gz);
         if (kept) {
           // zero terms (clamped alpha, low-pass pairs) skip their atomic
           float* sg = S.grad + j * SGRAD_STRIDE;
@@ -883,6 +941,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         }
         __syncwarp();
         if (end) S.tq[ps] = make_float2(Tb, tq.y + sum);
+        if constexpr (DIST)
+          if (end) S.ab[ps] = make_float2(ab.x + sa, ab.y + sb);
         __syncwarp();
       }
       };
@@ -895,6 +955,10 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         const float2 tq = S.tq[myslot];
         T = tq.x;
         Q = tq.y;
+        if constexpr (DIST) {
+          As = S.ab[myslot].x;
+          Bs = S.ab[myslot].y;
+        }
       }
       // flush this chunk's per-entry sums (decoded from fixed point where the
       // chunk used it): one set of vector atomics per entry; then gather the
@@ -1059,8 +1123,9 @@ static RenderArgs make_args(const Layout& L, const RastParams& P, char* ws, cons
   A.hdr = reinterpret_cast<Header*>(ws + L.header);
   A.tfinal = reinterpret_cast<float*>(ws + L.tfinal);
   A.last = reinterpret_cast<uint32_t*>(ws + L.last);
-  A.rgb = A.depth = A.normal = A.alpha = nullptr;
-  A.d_rgb = A.d_depth = A.d_normal = A.d_alpha = nullptr;
+  A.dfinal = reinterpret_cast<float*>(ws + L.dfinal);
+  A.rgb = A.depth = A.normal = A.alpha = A.dist = nullptr;
+  A.d_rgb = A.d_depth = A.d_normal = A.d_alpha = A.d_dist = nullptr;
   return A;
 }
 
@@ -1074,9 +1139,9 @@ static int persistent_grid(K kernel, int threads, size_t smem, int64_t work) {
   return (int)(g < 1 ? 1 : g);
 }
 
-template <int TW, int TH, int CHUNK>
-static cudaError_t run_fwd(const RenderArgs& A, cudaStream_t st) {
-  auto k = k_render_fwd<TW, TH, CHUNK>;
+template <int TW, int TH, int CHUNK, bool DIST>
+static cudaError_t run_fwd_k(const RenderArgs& A, cudaStream_t st) {
+  auto k = k_render_fwd<TW, TH, CHUNK, DIST>;
   constexpr size_t smem = sizeof(FwdSmem<TW * TH, CHUNK>);
   static int grid = -1;
   static int64_t grid_T = -1;
@@ -1090,9 +1155,13 @@ static cudaError_t run_fwd(const RenderArgs& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 template <int TW, int TH, int CHUNK>
-static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
-  auto k = k_render_bwd<TW, TH, CHUNK>;
-  constexpr size_t smem = sizeof(BwdSmem<TW * TH, CHUNK>);
+static cudaError_t run_fwd(const RenderArgs& A, cudaStream_t st) {
+  return A.dist ? run_fwd_k<TW, TH, CHUNK, true>(A, st) : run_fwd_k<TW, TH, CHUNK, false>(A, st);
+}
+template <int TW, int TH, int CHUNK, bool DIST>
+static cudaError_t run_bwd_k(const RenderArgs& A, cudaStream_t st) {
+  auto k = k_render_bwd<TW, TH, CHUNK, DIST>;
+  constexpr size_t smem = sizeof(BwdSmem<TW * TH, CHUNK, DIST>);
   static int grid = -1;
   static int64_t grid_T = -1;
   if (grid < 0) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1103,6 +1172,10 @@ static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
   k<<<grid, TW * TH, smem, st>>>(A);
   count_launches(1);
   return cudaGetLastError();
+}
+template <int TW, int TH, int CHUNK>
+static cudaError_t run_bwd(const RenderArgs& A, cudaStream_t st) {
+  return A.d_dist ? run_bwd_k<TW, TH, CHUNK, true>(A, st) : run_bwd_k<TW, TH, CHUNK, false>(A, st);
 }
 
 template <int TW, int TH>
@@ -1140,13 +1213,14 @@ static cudaError_t run_max_error(const RenderArgs& A, const float* err, uint32_t
   } while (0)
 
 cudaError_t launch_render_fwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
-                              float* rgb, float* depth, float* normal, float* alpha, cudaStream_t st) {
+                              float* rgb, float* depth, float* normal, float* alpha, float* dist, cudaStream_t st) {
   if (L.T <= 0) return cudaSuccess;
   RenderArgs A = make_args(L, P, ws, vals);
   A.rgb = rgb;
   A.depth = depth;
   A.normal = normal;
   A.alpha = alpha;
+  A.dist = dist;
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->queue_fwd, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
@@ -1155,13 +1229,14 @@ cudaError_t launch_render_fwd(const Layout& L, const RastParams& P, int chunk, c
 
 cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
                               const float* d_rgb, const float* d_depth, const float* d_normal,
-                              const float* d_alpha, cudaStream_t st) {
+                              const float* d_alpha, const float* d_dist, cudaStream_t st) {
   if (L.T <= 0) return cudaSuccess;
   RenderArgs A = make_args(L, P, ws, vals);
   A.d_rgb = d_rgb;
   A.d_depth = d_depth;
   A.d_normal = d_normal;
   A.d_alpha = d_alpha;
+  A.d_dist = d_dist;
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
   cudaError_t e = cudaMemsetAsync(&hdr->queue_bwd, 0, sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;

@@ -89,7 +89,7 @@ constexpr float kLn2 = 0.69314718055994531f;
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t header, views, groups, ntiles, records, rgrad, keys0, keys1, vals0, vals1, sort_hist, ranges,
-      tile_count, tile_order, tile_hist, tile_class, tfinal, last, rcopy, bmask, total;
+      tile_count, tile_order, tile_hist, tile_class, tfinal, last, dfinal, rcopy, bmask, total;
   int64_t bmask_words;  // 32-entry words of blended-pair masks (each holds one word per tile pixel)
   int64_t R, T, P, cap;
   int64_t n_work;     // sum over view groups of the surfel range sizes
@@ -136,10 +136,10 @@ cudaError_t launch_sort(uint64_t* keys0, uint32_t* vals0, uint64_t* keys1, uint3
                         const unsigned long long* n_dev, int64_t n_max, int key_bits, uint32_t* hist,
                         int sort_blocks, int* final_buffer, cudaStream_t st);
 cudaError_t launch_render_fwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
-                              float* rgb, float* depth, float* normal, float* alpha, cudaStream_t st);
+                              float* rgb, float* depth, float* normal, float* alpha, float* dist, cudaStream_t st);
 cudaError_t launch_render_bwd(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
                               const float* d_rgb, const float* d_depth, const float* d_normal,
-                              const float* d_alpha, cudaStream_t st);
+                              const float* d_alpha, const float* d_dist, cudaStream_t st);
 cudaError_t launch_max_error(const Layout& L, const RastParams& P, int chunk, char* ws, const uint32_t* vals,
                              const float* err, float* max_err, cudaStream_t st);
 cudaError_t launch_accum_gate(const float* alpha, int64_t n, float tau, uint32_t* keep_idx, int64_t* n_keep,

@@ -17,7 +17,8 @@ import torch
 
 from . import _abi
 
-__all__ = ["RasterConfig", "Rasterizer", "Images", "SurfelGrads", "Splat2DRender", "render", "accum_gate"]
+__all__ = ["RasterConfig", "Rasterizer", "Images", "SurfelGrads", "Splat2DRender", "Splat2DRenderDist", "render",
+           "accum_gate"]
 
 
 @dataclasses.dataclass
@@ -37,6 +38,18 @@ class RasterConfig:
     fwd_tail: int = 0  # 0: default; 255: forward always shares pixels across warps
     bwd_chunk: int = 64  # 0: same as chunk
     depth_ray: bool = False  # depth output from the ray-splat intersection (SPLAT2D_FLAG_DEPTH_RAY)
+
+    @classmethod
+    def for_problem(cls, views: Sequence, n_surfels: int, **kw) -> "RasterConfig":
+        """The default constants with the launch shape the autotuner keeps
+        for this problem's bucket (the user's cache, else the shipped GB300
+        measurement, else the defaults)."""
+        from . import autotune
+        cfg = cls(**kw)
+        tuned = autotune.lookup(views, n_surfels)
+        if tuned:
+            cfg.tile_w, cfg.tile_h, cfg.chunk, cfg.bwd_chunk = tuned
+        return cfg
 
     def to_c(self) -> _abi.Config:
         c = _abi.Config()
@@ -96,7 +109,8 @@ class Rasterizer:
     def __init__(self, views: Sequence, n_surfels: int, config: Optional[RasterConfig] = None,
                  capacity: Optional[int] = None, device=None):
         self.lib = _abi.load()
-        self.config = config or RasterConfig()
+        # no config: the autotuned launch shape of this problem's bucket
+        self.config = config or RasterConfig.for_problem(views, n_surfels)
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("the rasterizer runs on CUDA devices only")
@@ -228,28 +242,31 @@ class Rasterizer:
         _abi.check(self.lib.splat2d_bin_sort(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
                                              self.ws_bytes, _stream()), "splat2d_bin_sort")
 
-    def render_fwd(self, out: Images):
-        _abi.check(self.lib.splat2d_render_fwd(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
-                                               self.ws_bytes, _ptr(out.rgb), _ptr(out.depth), _ptr(out.normal),
-                                               _ptr(out.alpha), _stream()), "splat2d_render_fwd")
+    def render_fwd(self, out: Images, dist: Optional[torch.Tensor] = None):
+        """Forward compositing into `out`; with `dist` (one float per packed
+        pixel) also the depth distortion."""
+        _abi.check(self.lib.splat2d_render_fwd_dist(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
+                                                    self.ws_bytes, _ptr(out.rgb), _ptr(out.depth), _ptr(out.normal),
+                                                    _ptr(out.alpha), _ptr(dist), _stream()), "splat2d_render_fwd")
 
     def render_bwd(self, means, scales, quats, opacity, rgb, d_out: Sequence[Optional[torch.Tensor]],
-                   grads: SurfelGrads):
+                   grads: SurfelGrads, d_dist: Optional[torch.Tensor] = None):
         sf = self._surfels(means, scales, quats, opacity, rgb)
         g = _abi.Grads()
         g.means, g.scales, g.quats = _ptr(grads.means), _ptr(grads.scales), _ptr(grads.quats)
         g.opacity, g.rgb, g.pose = _ptr(grads.opacity), _ptr(grads.rgb), _ptr(grads.pose)
         d = [None if t is None else _ptr(t) for t in d_out]
-        _abi.check(self.lib.splat2d_render_bwd(ctypes.byref(self._cfg), ctypes.byref(self._prob), ctypes.byref(sf),
-                                               self._ws_ptr, self.ws_bytes, d[0], d[1], d[2], d[3], ctypes.byref(g),
-                                               _stream()), "splat2d_render_bwd")
+        _abi.check(self.lib.splat2d_render_bwd_dist(ctypes.byref(self._cfg), ctypes.byref(self._prob),
+                                                    ctypes.byref(sf), self._ws_ptr, self.ws_bytes, d[0], d[1], d[2],
+                                                    d[3], _ptr(d_dist), ctypes.byref(g), _stream()),
+                   "splat2d_render_bwd")
 
-    def render_bwd_tiles(self, d_out: Sequence[Optional[torch.Tensor]]):
+    def render_bwd_tiles(self, d_out: Sequence[Optional[torch.Tensor]], d_dist: Optional[torch.Tensor] = None):
         """Tile adjoint only: record gradients stay in the workspace."""
         d = [None if t is None else _ptr(t) for t in d_out]
-        _abi.check(self.lib.splat2d_render_bwd_tiles(ctypes.byref(self._cfg), ctypes.byref(self._prob), self._ws_ptr,
-                                                     self.ws_bytes, d[0], d[1], d[2], d[3], _stream()),
-                   "splat2d_render_bwd_tiles")
+        _abi.check(self.lib.splat2d_render_bwd_tiles_dist(ctypes.byref(self._cfg), ctypes.byref(self._prob),
+                                                          self._ws_ptr, self.ws_bytes, d[0], d[1], d[2], d[3],
+                                                          _ptr(d_dist), _stream()), "splat2d_render_bwd_tiles")
 
     def max_error(self, err: torch.Tensor, max_err: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Map-fusion pruning input: per surfel, the largest err over the
@@ -291,7 +308,7 @@ class Rasterizer:
         return int(rc)
 
     def forward(self, means, scales, quats, opacity, rgb, out: Optional[Images] = None, check: bool = True,
-                max_retries: int = 3) -> Images:
+                max_retries: int = 3, dist: Optional[torch.Tensor] = None) -> Images:
         """preprocess -> bin_sort -> render_fwd.  With check=True the device
         status is read (a synchronisation) and an instance-capacity overflow
         is repaired by growing the workspace and running again."""
@@ -299,7 +316,7 @@ class Rasterizer:
         for _ in range(max_retries + 1):
             self.preprocess(means, scales, quats, opacity, rgb)
             self.bin_sort()
-            self.render_fwd(out)
+            self.render_fwd(out, dist)
             if not check:
                 return out
             rc = self.status()
@@ -316,13 +333,15 @@ class Rasterizer:
         return SurfelGrads(z(n, 3), z(n, 2), z(n, 4), z(n), z(n, 3), z(self.n_views, 6))
 
     def backward(self, means, scales, quats, opacity, rgb, d_out: Sequence[Optional[torch.Tensor]],
-                 grads: Optional[SurfelGrads] = None) -> SurfelGrads:
-        """Gradients of sum(d_out . outputs); accumulated into `grads`
-        (zeros if not given).  d_out = (d_rgb, d_depth, d_normal, d_alpha),
-        packed like the forward outputs; None entries count as zero."""
+                 grads: Optional[SurfelGrads] = None, d_dist: Optional[torch.Tensor] = None) -> SurfelGrads:
+        """Gradients of sum(d_out . outputs) (+ sum(d_dist . distortion));
+        accumulated into `grads` (zeros if not given).  d_out = (d_rgb,
+        d_depth, d_normal, d_alpha), packed like the forward outputs; None
+        entries count as zero."""
         grads = grads or self.new_grads()
         flat = [None if t is None else t.contiguous().view(-1) for t in d_out]
-        self.render_bwd(means, scales, quats, opacity, rgb, flat, grads)
+        dd = None if d_dist is None else d_dist.contiguous().view(-1)
+        self.render_bwd(means, scales, quats, opacity, rgb, flat, grads, dd)
         return grads
 
 
@@ -381,8 +400,42 @@ class Splat2DRender(torch.autograd.Function):
         return (None, grads.means, grads.scales, grads.quats, grads.opacity, grads.rgb, grads.pose, None)
 
 
-def render(rast: Rasterizer, means, scales, quats, opacity, rgb, pose_tangent=None, check: bool = True):
-    """Functional form of Splat2DRender."""
+class Splat2DRenderDist(torch.autograd.Function):
+    """Splat2DRender that also returns the depth distortion map (the 2DGS
+    regulariser, see splat2d_render_fwd_dist): (rgb, depth, normal, alpha,
+    dist), dist shaped like alpha.  The same rules on the workspace apply."""
+
+    @staticmethod
+    def forward(ctx, rast: Rasterizer, means, scales, quats, opacity, rgb, pose_tangent, check: bool = True):
+        params = [t.contiguous() for t in (means, scales, quats, opacity, rgb)]
+        dist = torch.empty(rast.n_pixels, device=rast.device)
+        out = rast.forward(*params, check=check, dist=dist)
+        ctx.rast = rast
+        ctx.generation = rast.generation
+        ctx.save_for_backward(*params)
+        shaped = rast.shaped(out)
+        if rast.uniform:
+            H, W = rast.sizes[0]
+            dist = dist.view(rast.n_views, H, W)
+        return (*shaped, dist)
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_normal, g_alpha, g_dist):
+        rast: Rasterizer = ctx.rast
+        if rast.generation != ctx.generation:
+            raise RuntimeError("Splat2DRenderDist: the rasterizer ran another forward after this one, so its "
+                               "workspace no longer holds this render's state; use one Rasterizer per "
+                               "render that is differentiated")
+        params = ctx.saved_tensors
+        grads = rast.backward(*params, (g_rgb, g_depth, g_normal, g_alpha), d_dist=g_dist)
+        return (None, grads.means, grads.scales, grads.quats, grads.opacity, grads.rgb, grads.pose, None)
+
+
+def render(rast: Rasterizer, means, scales, quats, opacity, rgb, pose_tangent=None, check: bool = True,
+           distortion: bool = False):
+    """Functional form of Splat2DRender (with distortion=True, of
+    Splat2DRenderDist: the depth distortion map is a fifth output)."""
     if pose_tangent is None:
         pose_tangent = torch.zeros(rast.n_views, 6, device=means.device, requires_grad=False)
-    return Splat2DRender.apply(rast, means, scales, quats, opacity, rgb, pose_tangent, check)
+    fn = Splat2DRenderDist if distortion else Splat2DRender
+    return fn.apply(rast, means, scales, quats, opacity, rgb, pose_tangent, check)

@@ -53,3 +53,43 @@ def test_shipped_shapes_are_candidates_the_library_accepts():
         assert (tw, th) in tiles
         for depth in (ch, bch):
             assert depth in (64, 128, 256) or (depth == 512 and tw * th == 256)
+
+
+def test_tune_on_the_gpu(tmp_path):
+    """The tuner times every candidate launch shape on the GPU with real
+    forward + backward iterations, caches the fastest, and a rasterizer built
+    without a config takes it; every candidate renders the same images."""
+    import math
+
+    import numpy as np
+    import pytest
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_03092_gb300.rasterizer import RasterConfig, Rasterizer
+    sc = scenes.keyframe_scene(seed=1005, width=128, height=96, f=100.0, n_views=2)
+    params = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in
+              (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
+    P = sum(v.width * v.height for v in sc.views)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    d_out = (torch.randn(3 * P, device="cuda", generator=g), torch.randn(P, device="cuda", generator=g), None, None)
+    path = str(tmp_path / "tune.json")
+    import os
+    os.environ["SPLAT2D_AUTOTUNE_CACHE"] = path
+    try:
+        best, ms = autotune.tune(sc.views, sc.n, autotune.cuda_runner(sc.views, params, d_out), path=path)
+        assert best in [autotune._candidate(c) for c in autotune.CANDIDATES]
+        assert len(ms) == len(autotune.CANDIDATES) and all(math.isfinite(v) and v > 0 for v in ms.values())
+        rast = Rasterizer(sc.views, sc.n)  # no config: the cached choice
+        assert (rast.config.tile_w, rast.config.tile_h, rast.config.chunk, rast.config.bwd_chunk) == best
+        ref = Rasterizer(sc.views, sc.n, RasterConfig()).forward(*params)
+        for c in autotune.CANDIDATES:
+            c = autotune._candidate(c)
+            im = Rasterizer(sc.views, sc.n, RasterConfig(tile_w=c[0], tile_h=c[1], chunk=c[2], bwd_chunk=c[3])).forward(*params)
+            for a, b in zip(im, ref):
+                assert float((a - b).abs().max()) <= 1e-5, c
+    finally:
+        del os.environ["SPLAT2D_AUTOTUNE_CACHE"]
+
+
+test_tune_on_the_gpu = __import__("pytest").mark.gpu(test_tune_on_the_gpu)

@@ -485,3 +485,121 @@ def test_cuda_graph_replay_matches_eager():
         assert torch.equal(a, b)
     for a, b in zip(grads, g_eager):
         assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) < 1e-5
+
+
+# --------------------------------------------------------------------------
+# depth distortion (the 2DGS regulariser)
+# --------------------------------------------------------------------------
+
+DIST_ATOL = 2e-5  # FP32 accumulation of 2 w (z A - D) over up to ~150 blended pairs of depths up to 8 m
+
+
+@pytest.mark.parametrize("depth_ray", [False, True])
+def test_distortion_forward_matches_oracle(depth_ray):
+    sc = scenes.keyframe_scene(seed=1003, width=160, height=120, f=125.0, n_views=2)
+    cfg = RasterConfig(depth_ray=depth_ray)
+    params = to_dev(sc)
+    rast = Rasterizer(sc.views, sc.n, cfg)
+    dist = torch.empty(rast.n_pixels, device="cuda")
+    im = rast.forward(*params, dist=dist)
+    plain = Rasterizer(sc.views, sc.n, cfg).forward(*params)
+    for a, b in zip(im, plain):  # asking for the distortion changes no other output
+        assert torch.equal(a, b)
+    torch.cuda.synchronize()
+    flagged = total = 0
+    for v in range(len(sc.views)):
+        p = oracle.preprocess_scene_view(sc, v, oracle_cfg(cfg))
+        ref = oracle.render_dist(p)
+        fl = oracle.render(p).pflags
+        ok = (fl & (oracle.PF_FORWARD | (oracle.PF_BRANCH if depth_ray else 0))) == 0
+        H, W = sc.views[v].height, sc.views[v].width
+        o = int(rast._cviews[v].pixel_offset)
+        gpu = dist[o:o + H * W].view(H, W).cpu().numpy().astype(np.float64)
+        err = np.abs(gpu - ref)[ok]
+        assert err.max() <= DIST_ATOL, (v, err.max())
+        assert ref.max() > 1e-2
+        flagged += int((~ok).sum())
+        total += ok.size
+    print(f"flagged {flagged}/{total}")
+    assert flagged <= 1.2e-3 * total
+
+
+@pytest.mark.parametrize("depth_ray", [False, True])
+def test_distortion_backward_matches_oracle(depth_ray):
+    sc = scenes.random_scene(n=3000, width=96, height=72, f=70.0, seed=40 + int(depth_ray), n_views=2,
+                             scale_range=(0.03, 0.2))
+    cfg = RasterConfig(depth_ray=depth_ray, bg=(0.2, 0.1, 0.3))
+    params = to_dev(sc)
+    rast = Rasterizer(sc.views, sc.n, cfg)
+    rast.forward(*params, dist=torch.empty(rast.n_pixels, device="cuda"))
+    d_dev, d_views = upstream(rast, 3)
+    rng = np.random.default_rng(4)
+    gd_views = [rng.normal(size=(h, w)) * 5.0 for (h, w) in rast.sizes]
+    gd = torch.from_numpy(np.concatenate([g.reshape(-1) for g in gd_views]).astype(np.float32)).cuda()
+    grads = rast.backward(*params, d_dev, d_dist=gd)
+    torch.cuda.synchronize()
+    og, poses = None, []
+    for v in range(len(sc.views)):
+        p = oracle.preprocess_scene_view(sc, v, oracle_cfg(cfg))
+        gv = oracle.render_bwd(sc.means, sc.scales, sc.quats, p, d_views[v], g_dist=gd_views[v])
+        poses.append(gv.pose)
+        if og is None:
+            og = gv
+        else:
+            for name in ("means", "scales", "quats", "opacity", "rgb"):
+                setattr(og, name, getattr(og, name) + getattr(gv, name))
+    out = {name: rel_l2(getattr(grads, name).cpu().numpy(), getattr(og, name))
+           for name in ("means", "scales", "quats", "opacity", "rgb")}
+    out["pose"] = max(rel_l2(grads.pose.cpu().numpy()[v], poses[v]) for v in range(len(sc.views)))
+    print(out)
+    for k, e in out.items():
+        assert e <= GRAD_REL_L2, (k, out)
+
+
+def test_distortion_through_autograd():
+    """render(..., distortion=True) returns the distortion map as a fifth
+    output and its backward equals the direct call with that upstream."""
+    sc = scenes.keyframe_scene(seed=1004, width=96, height=72, f=75.0, n_views=2)
+    params = [p.clone().requires_grad_(True) for p in to_dev(sc)]
+    rast = Rasterizer(sc.views, sc.n, RasterConfig())
+    outs = render(rast, *params, distortion=True)
+    assert len(outs) == 5 and outs[4].shape == outs[3].shape
+    w = [torch.randn_like(t) for t in outs]
+    sum((a * b).sum() for a, b in zip(w, outs)).backward()
+    direct = rast.backward(*[p.detach() for p in params], [x.contiguous() for x in w[:4]], d_dist=w[4].contiguous())
+    for p, g in zip(params, direct):
+        assert rel_l2(p.grad.cpu().numpy(), g.cpu().numpy()) < 1e-5
+
+
+def test_normal_consistency_identity_on_rendered_maps():
+    """The normal-consistency term of the 2DGS geometry, sum_i w_i (1 - n_i.N)
+    for a reference normal N, is a function of the rendered maps: A - N_hat.N.
+    Surfels of different orientations whose centers project onto one pixel
+    center have alpha = sigma there whatever their tilt, so their weights and
+    normals are known in closed form; the GPU's maps give the same value."""
+    view = scenes.View(24, 20, 30.0, 30.0, 12.0, 10.0, np.concatenate([np.eye(3), np.zeros((3, 1))], 1).astype(np.float32))
+    ix, iy = 9, 7
+    z = np.array([2.0, 2.5, 3.1])
+    sig = np.array([0.4, 0.55, 0.7], np.float32)
+    mu = np.stack([(ix + 0.5 - view.cx) * z / view.fx, (iy + 0.5 - view.cy) * z / view.fy, z], 1).astype(np.float32)
+    from scipy.spatial.transform import Rotation
+    rots = [Rotation.from_rotvec(r) for r in ([0.3, 0.0, 0.1], [-0.2, 0.4, 0.0], [0.1, -0.1, 0.5])]
+    q = np.array([[r.as_quat()[3], *r.as_quat()[:3]] for r in rots], np.float32)
+    sc = scenes.Scene(mu, np.full((3, 2), 0.05, np.float32), q, sig, np.ones((3, 3), np.float32), [view])
+    rast, params, im = gpu_forward(sc, RasterConfig())
+    s = sig.astype(np.float64)
+    w = np.array([s[0], s[1] * (1 - s[0]), s[2] * (1 - s[0]) * (1 - s[1])])
+    n = []
+    for r, m in zip(rots, mu.astype(np.float64)):
+        nv = Rotation.from_quat(r.as_quat().astype(np.float32).astype(np.float64)).as_matrix()[:, 2]
+        n.append(-nv if nv @ m > 0 else nv)
+    n = np.array(n)
+    N = np.array([0.2, -0.3, -0.93])
+    N /= np.linalg.norm(N)
+    want = float((w * (1.0 - n @ N)).sum())
+    g = view_stack(rast, im, 0)
+    got = g[7, iy, ix] - g[4:7, iy, ix] @ N
+    assert abs(got - want) <= 1e-5, (got, want)
+    p = oracle.preprocess(sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb, view, oracle.Config(tile_w=8, tile_h=8))
+    o = oracle.render(p).out
+    assert abs(o[7, iy, ix] - o[4:7, iy, ix] @ N - want) <= 1e-9

@@ -37,6 +37,12 @@ MUTATIONS = [
      "dM[i * 3 + j] += gr[R_DET] * g.A[i * 3 + j];"),
     ("ray depth where the low-pass term decides", "e->zray = cfg->depth_ray && e->obj && e->c != 0;",
      "e->zray = cfg->depth_ray && e->c != 0;"),
+    ("distortion: factor 2 dropped", "d += 2.0 * wi * wj * (list[i].e.z - list[j].e.z);",
+     "d += wi * wj * (list[i].e.z - list[j].e.z);"),
+    ("distortion adjoint: terms behind the entry dropped", "const double Wk = 2.0 * (zi * Ap - Bp + Bsuf - zi * Asuf);",
+     "const double Wk = 2.0 * (zi * Ap - Bp);"),
+    ("distortion adjoint: depth gradient sign", "dzd = gd * 2.0 * w * (Ap - Asuf);", "dzd = gd * 2.0 * w * (Asuf - Ap);"),
+    ("distortion adjoint: transmittance term", "da += gd * (Wk * Ti - Wsuf / om);", "da += gd * (Wk * Ti);"),
     ("error attribution summed", "if (e > max_err[list[k].s]) max_err[list[k].s] = e;",
      "max_err[list[k].s] += e;"),
 ]

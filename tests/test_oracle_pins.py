@@ -724,3 +724,145 @@ def test_rigid_gradient_identities():
     rhs = R.T @ (g.pose[3:] - np.cross(t, g.pose[:3]))
     # exact for an orthogonal R; the FP32 camera rotation is orthogonal to ~1e-7
     np.testing.assert_allclose(lhs, rhs, rtol=2e-7, atol=1e-8)
+
+
+# --------------------------------------------------------------------------
+# depth distortion (the 2DGS regulariser): closed forms, invariants, FD
+# --------------------------------------------------------------------------
+
+def test_distortion_closed_form_stacked_surfels():
+    """Surfels parallel to the image plane whose centers project onto the
+    same pixel center have alpha = sigma there, so the blended weights are
+    w_1 = s_1, w_2 = s_2 (1 - s_1), w_3 = s_3 (1 - s_1)(1 - s_2) in depth
+    order, and the distortion at that pixel is
+    2 [w_2 w_1 (z_2 - z_1) + w_3 w_1 (z_3 - z_1) + w_3 w_2 (z_3 - z_2)]."""
+    view = _view(W=24, H=20, f=30.0)
+    ix, iy = 9, 7
+    z = np.array([2.0, 2.6, 3.3])
+    sig = np.array([0.5, 0.35, 0.8])
+    mu = np.stack([(ix + 0.5 - view.cx) * z / view.fx, (iy + 0.5 - view.cy) * z / view.fy, z], 1)
+    # listed out of depth order: the sort decides
+    order = [2, 0, 1]
+    p = oracle.preprocess(mu[order].astype(np.float32), np.full((3, 2), 0.05, np.float32),
+                          np.tile(np.array([1.0, 0, 0, 0], np.float32), (3, 1)), sig[order].astype(np.float32),
+                          np.ones((3, 3), np.float32), view, oracle.Config())
+    d = oracle.render_dist(p)
+    s32 = sig.astype(np.float32).astype(np.float64)
+    z32 = mu[:, 2].astype(np.float32).astype(np.float64)
+    w = np.array([s32[0], s32[1] * (1 - s32[0]), s32[2] * (1 - s32[0]) * (1 - s32[1])])
+    want = 2 * (w[1] * w[0] * (z32[1] - z32[0]) + w[2] * w[0] * (z32[2] - z32[0]) + w[2] * w[1] * (z32[2] - z32[1]))
+    assert d[iy, ix] == pytest.approx(want, rel=1e-9)
+    # one surfel alone has no distortion anywhere
+    p1 = oracle.preprocess(mu[:1].astype(np.float32), np.full((1, 2), 0.05, np.float32),
+                           np.array([[1.0, 0, 0, 0]], np.float32), sig[:1].astype(np.float32),
+                           np.ones((1, 3), np.float32), view, oracle.Config())
+    assert np.abs(oracle.render_dist(p1)).max() == 0.0
+
+
+def test_distortion_invariants():
+    """A rigid motion of surfels and camera leaves the distortion unchanged
+    (depth differences along the optical axis are preserved); a similarity
+    scale s of surfels, their scales and the camera translation scales it by
+    s; it is never negative with the center depth (the sort key)."""
+    sc, cfg, _ = _loss_setup(5, n=64)
+    cfg = oracle.Config()
+    p = oracle.preprocess_scene_view(sc, 0, cfg)
+    d0 = oracle.render_dist(p)
+    assert d0.max() > 1e-3 and d0.min() >= 0.0
+    Rg = Rotation.from_rotvec([0.1, -0.2, 0.05]).as_matrix()
+    tg = np.array([0.3, -0.1, 0.2])
+    R, t = sc.views[0].Rt[:, :3].astype(np.float64), sc.views[0].Rt[:, 3].astype(np.float64)
+    means2 = (sc.means.astype(np.float64) @ Rg.T + tg).astype(np.float32)
+    qg = Rotation.from_matrix(Rg).as_quat()
+    qg = np.array([qg[3], qg[0], qg[1], qg[2]])
+    q = sc.quats.astype(np.float64)
+    w0, v0 = qg[0], qg[1:]
+    qw, qv = q[:, :1], q[:, 1:]
+    quats2 = np.concatenate([w0 * qw - qv @ v0[:, None], w0 * qv + qw * v0 + np.cross(v0, qv)], 1).astype(np.float32)
+    R2 = R @ Rg.T
+    t2 = t - R2 @ tg
+    v2 = copy.copy(sc.views[0])
+    v2.Rt = np.concatenate([R2, t2[:, None]], 1).astype(np.float32)
+    p2 = oracle.preprocess(means2, sc.scales, quats2, sc.opacity, sc.rgb, v2, cfg)
+    d2 = oracle.render_dist(p2)
+    ok = ((oracle.render(p).pflags | oracle.render(p2).pflags) & oracle.PF_FORWARD) == 0
+    np.testing.assert_allclose(d2[ok], d0[ok], atol=1e-5)
+    s = 1.7
+    v3 = copy.copy(sc.views[0])
+    v3.Rt = np.concatenate([R, (s * t)[:, None]], 1).astype(np.float32)
+    p3 = oracle.preprocess((s * sc.means.astype(np.float64)).astype(np.float32),
+                           (s * sc.scales.astype(np.float64)).astype(np.float32), sc.quats, sc.opacity, sc.rgb, v3, cfg)
+    d3 = oracle.render_dist(p3)
+    ok = ((oracle.render(p).pflags | oracle.render(p3).pflags) & oracle.PF_FORWARD) == 0
+    np.testing.assert_allclose(d3[ok], s * d0[ok], rtol=1e-4, atol=1e-6)
+
+
+@pytest.mark.parametrize("seed,depth_ray", [(0, False), (3, True)])
+def test_distortion_gradient_matches_central_differences(seed, depth_ray):
+    """Analytic gradient of L = sum(g . outputs) + sum(g_d . distortion)
+    w.r.t. every parameter vs FP64 central differences (parameters whose
+    step flips a discrete decision are skipped), with the center depth and
+    with the per-pixel ray depth."""
+    sc, cfg, g8 = _loss_setup(seed, depth_ray=depth_ray)
+    gd = np.random.default_rng(seed + 7).normal(size=g8.shape[1:]) * 3.0
+    p = oracle.preprocess_scene_view(sc, 0, cfg)
+    g = oracle.render_bwd(sc.means, sc.scales, sc.quats, p, g8, g_dist=gd)
+
+    def loss(s2):
+        q = oracle.preprocess(s2.means, s2.scales, s2.quats, s2.opacity, s2.rgb, s2.views[0], cfg)
+        im = oracle.render(q)
+        return float((g8 * im.out).sum() + (gd * oracle.render_dist(q)).sum()), im.phash
+    checked = 0
+    for name in ("means", "scales", "quats", "opacity", "rgb"):
+        arr = getattr(sc, name)
+        an = getattr(g, name).reshape(-1)
+        for i in range(arr.size):
+            v0 = float(arr.reshape(-1)[i])
+            h = 2e-5 * max(1.0, abs(v0))  # the ray depth (1 / c) curves more: a smaller step
+            res = []
+            for sgn in (1, -1):
+                s2 = copy.copy(sc)
+                a2 = arr.copy()
+                a2.reshape(-1)[i] = np.float32(v0 + sgn * h)
+                setattr(s2, name, a2)
+                L, ph = loss(s2)
+                res.append((L, float(a2.reshape(-1)[i]), ph))
+            if not np.array_equal(res[0][2], res[1][2]):
+                continue
+            fd = (res[0][0] - res[1][0]) / (res[0][1] - res[1][1])
+            assert abs(fd - an[i]) <= 2e-4 * abs(an[i]) + 2e-4, (name, i, an[i], fd)
+            checked += 1
+    assert checked > 300
+    # the distortion term is not negligible in this loss
+    g0 = oracle.render_bwd(sc.means, sc.scales, sc.quats, p, g8)
+    assert np.abs(g.means - g0.means).max() > 1e-2 * np.abs(g0.means).max()
+
+
+def test_normal_consistency_identity_closed_form():
+    """sum_i w_i (1 - n_i.N) = A - N_hat.N: the normal-consistency term of the
+    2DGS geometry is a function of the rendered alpha and normal maps.  Three
+    surfels of different tilts whose centers project onto one pixel center
+    have alpha = sigma there whatever their tilt, so their weights (sigma_1,
+    sigma_2 (1 - sigma_1), ...) and normals (turned to face the camera) are
+    known in closed form."""
+    view = _view(W=24, H=20, f=30.0)
+    ix, iy = 9, 7
+    z = np.array([2.0, 2.5, 3.1])
+    sig = np.array([0.4, 0.55, 0.7], np.float32)
+    mu = np.stack([(ix + 0.5 - view.cx) * z / view.fx, (iy + 0.5 - view.cy) * z / view.fy, z], 1).astype(np.float32)
+    rots = [Rotation.from_rotvec(r) for r in ([0.3, 0.0, 0.1], [-0.2, 0.4, 0.0], [0.1, -0.1, 0.5])]
+    q = np.array([[r.as_quat()[3], *r.as_quat()[:3]] for r in rots], np.float32)
+    p = oracle.preprocess(mu, np.full((3, 2), 0.05, np.float32), q, sig, np.ones((3, 3), np.float32), view,
+                          oracle.Config())
+    o = oracle.render(p).out
+    s = sig.astype(np.float64)
+    w = np.array([s[0], s[1] * (1 - s[0]), s[2] * (1 - s[0]) * (1 - s[1])])
+    n = []
+    for qq, m in zip(q.astype(np.float64), mu.astype(np.float64)):
+        nv = _rot(qq)[:, 2]
+        n.append(-nv if nv @ m > 0 else nv)
+    n = np.array(n)
+    for N in (np.array([0.2, -0.3, -0.93]), np.array([0.0, 0.0, -1.0]), n[1]):
+        N = N / np.linalg.norm(N)
+        want = float((w * (1.0 - n @ N)).sum())
+        assert o[7, iy, ix] - o[4:7, iy, ix] @ N == pytest.approx(want, abs=1e-9)
