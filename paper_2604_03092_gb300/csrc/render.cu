@@ -372,8 +372,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
         if (__all_sync(0xffffffffu, done)) {
+          // streaming stores: read once, by the backward, long after
           uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
-          for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(size_t)w2 * NT] = 0u;
+          for (int w2 = 0; w2 < nwd && bm_ok; w2++) __stcs(bm + (size_t)w2 * NT, 0u);
           continue;
         }
         for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
@@ -420,7 +421,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         S.bits[wid][wd][lane] = bl;
         for (int w2 = wd + 1; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;
         uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
-        for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(size_t)w2 * NT] = S.bits[wid][w2][lane];
+        for (int w2 = 0; w2 < nwd && bm_ok; w2++) __stcs(bm + (size_t)w2 * NT, S.bits[wid][w2][lane]);
       } else {
         // ---- tail: warps pull the remaining pixels; a warp composites 32 of
         //      a pixel's entries per step with a prefix product of (1 - alpha)
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         }
         __syncthreads();
         uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
-        for (int w2 = 0; w2 < nwd && bm_ok; w2++) bm[(size_t)w2 * NT] = S.bits[wid][w2][lane];
+        for (int w2 = 0; w2 < nwd && bm_ok; w2++) __stcs(bm + (size_t)w2 * NT, S.bits[wid][w2][lane]);
         if (!done) {
           const FwdState st = S.st[threadIdx.x];
           T = st.T; C0 = st.C0; C1 = st.C1; C2 = st.C2; D = st.D;
@@ -785,7 +786,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         for (int wd = 0; wd < NWD; wd++) {
           uint32_t m = 0;
           if (wd < nwd) {
-            m = (act && bm_ok) ? __ldg(bm + (int64_t)wd * NT) : 0u;
+            m = (act && bm_ok) ? __ldcs(bm + (int64_t)wd * NT) : 0u;  // read once
             S.pbits[myslot][wd] = m;
           }
           pc[wd] = __popc(m);
