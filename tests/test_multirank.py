@@ -142,11 +142,15 @@ def test_two_gloo_ranks_sum_view_sharded_surfel_gradients(tmp_path):
         ref_pose[v] = ref.pose.copy()
         ref.pose[:] = 0.0
     got = [np.load(tmp_path / f"rank{r}.npz") for r in range(world)]
+    # FP64 sums in another order (the oracle accumulates with OpenMP atomics,
+    # the exchange adds the two ranks' partial sums): equal to ~1e-13 of the
+    # largest term, so the bound is set well above that and far below any
+    # missing or doubled view's contribution
     for name, _ in multirank.SURFEL_GRAD_FIELDS:
         want = getattr(ref, name)
         assert np.count_nonzero(want) > 0
         for r in range(world):
-            np.testing.assert_allclose(got[r][name], want, rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(got[r][name], want, rtol=1e-9, atol=1e-11 * np.abs(want).max())
     for r in range(world):
         for v in multirank.view_shard(len(sc.views), r, world):
-            np.testing.assert_allclose(got[r][f"pose{v}"], ref_pose[v], rtol=1e-12, atol=1e-14)
+            np.testing.assert_allclose(got[r][f"pose{v}"], ref_pose[v], rtol=1e-9, atol=1e-11 * np.abs(ref_pose[v]).max())
