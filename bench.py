@@ -449,9 +449,12 @@ def main():
         d_rgb = (torch.sign(shaped.rgb - trgb) / trgb.numel()).contiguous().view(-1)
         d_depth = (0.1 * torch.sign(shaped.depth - tdep) / tdep.numel()).contiguous().view(-1)
     else:
+        # no targets (views of different sizes): the same L1 RGB + 0.1 L1
+        # depth gradient with random signs standing in for sign(render - target)
         gen = torch.Generator(device=dev).manual_seed(0)
-        d_rgb = torch.randn(3 * rast.n_pixels, device=dev, generator=gen) * 1e-6
-        d_depth = torch.randn(rast.n_pixels, device=dev, generator=gen) * 1e-7
+        P = rast.n_pixels
+        d_rgb = torch.sign(torch.randn(3 * P, device=dev, generator=gen)) / (3 * P)
+        d_depth = 0.1 * torch.sign(torch.randn(P, device=dev, generator=gen)) / P
     d_out = (d_rgb, d_depth, None, None)
     out = rast.new_images()
     grads = rast.new_grads()

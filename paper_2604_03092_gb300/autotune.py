@@ -24,11 +24,13 @@ CANDIDATES: List[Candidate] = [(16, 16, 256, 256), (16, 16, 128, 128), (16, 16, 
                                (8, 8, 128, 128), (8, 8, 128, 64), (8, 8, 256, 64), (32, 8, 256, 256),
                                (32, 8, 128, 128)]
 
-# Best launch shapes measured on GB300 (forward + backward step time over the
-# candidates above), by bucket: one 512x384 keyframe seen from 8 views
-# (img18_dens0), 64 uneven submaps at 320x240..640x480 (img18_dens1), 8- and
-# 32-keyframe submaps at 512x384 (img18_dens3, img18_dens5).
-SHIPPED: Dict[str, Candidate] = {"img18_dens0": (8, 8, 128, 64), "img18_dens1": (8, 8, 128, 64),
+# Best launch shapes measured on GB300 by tune() with cuda_runner (forward +
+# backward step time over the candidates above), by bucket: one 512x384
+# keyframe seen from 8 views (img18_dens0), 64 uneven submaps at
+# 320x240..640x480 (img18_dens1: 8x8/64/64 91.8 ms, 8x8/128/64 93.2 ms),
+# 8- and 32-keyframe submaps at 512x384 (img18_dens3, img18_dens5:
+# 8x8/64/64 70.3 ms, 8x8/128/64 72.0 ms, 16x16/256/256 107.9 ms).
+SHIPPED: Dict[str, Candidate] = {"img18_dens0": (8, 8, 128, 64), "img18_dens1": (8, 8, 64, 64),
                                  "img18_dens3": (8, 8, 64, 64), "img18_dens5": (8, 8, 64, 64)}
 
 
