@@ -878,8 +878,10 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           const float4 nrm = S.rec.n[j];
           f = fmaf(u1.x, nrm.x, fmaf(u1.y, nrm.y, fmaf(u1.z, nrm.z, f)));
         }
-        float dzd = 0.f, sa = 0.f, sb = 0.f;  // distortion: its depth gradient; the run's sums of w, w z
-        float2 ab = make_float2(0.f, 0.f);
+        // distortion only: its depth gradient; the run's sums of w and w z; the pixel's carried sums
+        float dzd = 0.f;
+        [[maybe_unused]] float sa = 0.f, sb = 0.f;
+        [[maybe_unused]] float2 ab = make_float2(0.f, 0.f);
         if constexpr (DIST) {
           // segmented prefix sums of w and w z: with the pixel's carried
           // sums, those behind this pair
