@@ -171,6 +171,52 @@ def oracle_views(sc, views, seed: int = 0):
     return wall / len(views), desc, wall
 
 
+def oracle_timing_child():
+    """Child-process body of `oracle_timing` (OpenMP fixes its thread count
+    at load): prints one JSON object with the seconds the oracle takes, as it
+    stands, for the forward and reverse pass (with the chain rule) of the
+    4,096-surfel random scene in definition mode (every surfel at every
+    pixel) and of all 8 views of the 512x384 keyframe workload (binned)."""
+    import oracle
+    from paper_2604_03092_gb300 import scenes
+
+    def fb(sc, v, mode, cfg):
+        H, W = sc.views[v].height, sc.views[v].width
+        p = oracle.preprocess_scene_view(sc, v, cfg)
+        oracle.render(p, mode)
+        off, cnt = sc.view_ranges()[v]
+        sl = slice(off, off + cnt)
+        up = np.random.default_rng(v).normal(size=(8, H, W))
+        oracle.render_bwd(sc.means[sl], sc.scales[sl], sc.quats[sl], p, up, mode=mode)
+    sc0 = scenes.random_scene(n=4096, seed=0)
+    t0 = time.perf_counter()
+    fb(sc0, 0, 0, oracle.Config())
+    t_def = time.perf_counter() - t0
+    sc1 = scenes.keyframe_scene(seed=1001)
+    t0 = time.perf_counter()
+    for v in range(len(sc1.views)):
+        fb(sc1, v, 1, oracle.Config(tile_w=8, tile_h=8))
+    t_kf = time.perf_counter() - t0
+    print(json.dumps({"random4096_definition_s": t_def, "keyframe8_all_views_s": t_kf,
+                      "threads": _omp_threads()}), flush=True)
+
+
+def oracle_timing() -> dict:
+    """The oracle's breadth timings, 1 thread and all host cores (child
+    processes): definition mode on the 4,096-surfel scene, and the 8-view
+    512x384 keyframe workload.  About 20 s in all."""
+    res = {}
+    for label, threads in (("threads_1", 1), ("threads_all", os.cpu_count() or 1)):
+        env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+        r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-timing-child"], env=env,
+                           capture_output=True, text=True, timeout=600)
+        try:
+            res[label] = json.loads(r.stdout.strip().splitlines()[-1])
+        except (ValueError, IndexError):
+            res[label] = {"failed": r.stderr[-300:]}
+    return res
+
+
 def _omp_threads() -> int:
     return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
@@ -387,7 +433,12 @@ def main():
     ap.add_argument("--cpu-views", type=int, default=4, help="whole views the oracle CPU baseline renders (~3 s each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-maintenance", action="store_true", help="skip timing the map-maintenance kernels")
+    ap.add_argument("--oracle-timing-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--spatial-order", action="store_true",
+                    help="store each 512x384 keyframe's surfels in 8x8 tile-blocked order (scenes.reorder_keyframes)")
     args = ap.parse_args()
+    if args.oracle_timing_child:
+        return oracle_timing_child()
     args.warmup = max(args.warmup, 3)
 
     wls = _workloads()
@@ -412,6 +463,9 @@ def main():
     torch.cuda.set_device(dev)
 
     sc = make(multirank.submap_seed_offset(rank))  # each rank: its own independent submap
+    if args.spatial_order:
+        from paper_2604_03092_gb300 import scenes as _sc
+        sc = _sc.reorder_keyframes(sc, 512, 384)
     V = len(sc.views)
     params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
               (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]
@@ -751,7 +805,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         per_view, desc, _ = oracle_views(sc, list(range(min(args.cpu_views, len(sc.views)))))
         cpu = {"value": 1.0 / per_view, "unit": "views/s", "cores": _omp_threads(), "kind": "oracle",
-               "sample": desc}
+               "sample": desc, "breadth": oracle_timing()}
 
     if rank == 0:
         line = {

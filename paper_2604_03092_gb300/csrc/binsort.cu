@@ -515,182 +515,6 @@ __device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restr
   return r;
 }
 
-// Register radix pass over 32-bit ranking keys ((top relative-depth bits) <<
-// 16 | position in the bucket): block_radix_reg's ballot multisplit and
-// block scan with the digits taken from bits 16 + 8 pass.  Stable, so keys
-// that tie on those bits keep their bucket order.  Returns the buffer holding
-// the result (a or b).
-template <int NWARPS, int ITEMS>
-__device__ uint32_t* block_radix_reg32(uint32_t* a, uint32_t* b, int n, uint16_t* cnt, uint32_t* tot, int passes) {
-  constexpr int NT = NWARPS * 32, CP = RegSortSmem<NWARPS>::CP;
-  static_assert(NWARPS % 8 == 0, "the counter scan takes 8 counters per thread");
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t lt_mask = (1u << lane) - 1u;
-  const int per = (((n + NWARPS - 1) / NWARPS) + 31) & ~31;
-  const int lo = min(wid * per, n), hi = min(lo + per, n);
-  const int nr = (hi - lo + 31) >> 5;  // rounds of this warp (<= ITEMS)
-  uint32_t* src = a;
-  uint32_t* dst = b;
-  for (int pass = 0; pass < passes; pass++) {
-    const int shift = 16 + 8 * pass;
-    uint32_t key[ITEMS], off[ITEMS];
-#pragma unroll
-    for (int k = 0; k < ITEMS; k++) {
-      const int i = lo + k * 32 + lane;
-      key[k] = (k < nr && i < hi) ? src[i] : 0u;
-    }
-    for (int i = threadIdx.x; i < 256 * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < ITEMS; k++) {
-      if (k < nr) {
-        const bool valid = lo + k * 32 + lane < hi;
-        const uint32_t d = valid ? (key[k] >> shift) & 0xffu : 0u;
-        uint32_t peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-        for (int bit = 0; bit < 8; bit++) {
-          const bool on = (d >> bit) & 1u;
-          const uint32_t bal = __ballot_sync(0xffffffffu, on);
-          peers &= on ? bal : ~bal;
-        }
-        const int leader = __ffs(peers) - 1;
-        uint32_t pre = 0;
-        if (valid && lane == leader) {
-          pre = cnt[d * CP + wid];
-          cnt[d * CP + wid] = (uint16_t)(pre + __popc(peers));
-        }
-        pre = __shfl_sync(0xffffffffu, pre, leader & 31);
-        off[k] = (d << 16) | (pre + __popc(peers & lt_mask));
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    {
-      // exclusive scan of the counters in (digit, warp) order, 8 per thread
-      const int f0 = 8 * threadIdx.x, d = f0 / NWARPS, w0 = f0 % NWARPS;
-      uint32_t c[8], sum = 0;
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        c[j] = cnt[d * CP + w0 + j];
-        sum += c[j];
-      }
-      uint32_t x = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane == 31) tot[wid] = x;
-      __syncthreads();
-      if (wid == 0) {
-        uint32_t y = lane < NWARPS ? tot[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-          if (lane >= o) y += z;
-        }
-        if (lane < NWARPS) tot[lane] = y;
-      }
-      __syncthreads();
-      uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
-#pragma unroll
-      for (int j = 0; j < 8; j++) {
-        cnt[d * CP + w0 + j] = (uint16_t)ex;
-        ex += c[j];
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < ITEMS; k++) {
-      if (k < nr && lo + k * 32 + lane < hi) {
-        const uint32_t d = off[k] >> 16;
-        dst[(uint32_t)cnt[d * CP + wid] + (off[k] & 0xffffu)] = key[k];
-      }
-    }
-    __syncthreads();
-    uint32_t* t = src;
-    src = dst;
-    dst = t;
-  }
-  return src;
-}
-
-// Sort a bucket of at most NWARPS * 32 * ITEMS composites (depth bits << 32 |
-// surfel index, in global memory) by (depth bits, surfel index) and write the
-// tile's sorted keys and values.  Ranking keys of 32 bits -- the top 16 bits
-// of the depth relative to the bucket's smallest, and the entry's position in
-// the bucket -- are radix-sorted in shared memory (one or two passes); each
-// run of entries that tie on those bits is then put in (depth, surfel) order
-// by one thread from the composites, and every entry is written straight to
-// the output.  Returns false, with nothing valid written, if some run is
-// longer than 64 (a wall of equal depths): the caller sorts that bucket
-// another way.
-template <int NWARPS, int ITEMS>
-__device__ bool sort_bucket_reg32(const unsigned long long* __restrict__ g, int n, uint32_t* sa, uint32_t* sb,
-                                  uint16_t* cnt, uint32_t* tot, uint32_t* red, uint64_t tile,
-                                  uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  constexpr int NT = NWARPS * 32;
-  if (threadIdx.x == 0) {
-    red[0] = 0xffffffffu; red[1] = 0u; red[4] = 0u;
-  }
-  __syncthreads();
-  uint32_t dmn = 0xffffffffu, dmx = 0u;
-  for (int i = threadIdx.x; i < n; i += NT) {
-    const uint32_t d = (uint32_t)(g[i] >> 32);
-    dmn = min(dmn, d);
-    dmx = max(dmx, d);
-  }
-  dmn = __reduce_min_sync(0xffffffffu, dmn);
-  dmx = __reduce_max_sync(0xffffffffu, dmx);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(&red[0], dmn);
-    atomicMax(&red[1], dmx);
-  }
-  __syncthreads();
-  const uint32_t dmin = red[0];
-  const int dbits = bits_of(red[1] - red[0]);
-  const int lsb = max(dbits - 16, 0);
-  for (int i = threadIdx.x; i < n; i += NT)
-    sa[i] = ((((uint32_t)(g[i] >> 32) - dmin) >> lsb) << 16) | (uint32_t)i;
-  __syncthreads();
-  const uint32_t* r = block_radix_reg32<NWARPS, ITEMS>(sa, sb, n, cnt, tot, (dbits - lsb + 7) >> 3);
-  auto top = [&](int i) -> uint32_t { return r[i] >> 16; };
-  for (int i = threadIdx.x; i < n; i += NT) {
-    const uint32_t d = top(i);
-    const bool prev = i > 0 && top(i - 1) == d, next = i + 1 < n && top(i + 1) == d;
-    if (!prev && !next) {
-      const unsigned long long c = g[r[i] & 0xffffu];
-      keys[i] = tile | (c >> 32);
-      vals[i] = (uint32_t)c;
-      continue;
-    }
-    if (prev) continue;  // inside a run: its first entry's thread writes it
-    int e = i + 1;
-    while (e + 1 < n && e - i < 64 && top(e + 1) == d) e++;
-    if (e + 1 < n && top(e + 1) == d) {
-      red[4] = 1u;
-      continue;
-    }
-    unsigned long long run[65];
-    const int m = e - i + 1;
-    for (int x = 0; x < m; x++) {
-      const unsigned long long c = g[r[i + x] & 0xffffu];
-      int y = x - 1;
-      while (y >= 0 && run[y] > c) {
-        run[y + 1] = run[y];
-        y--;
-      }
-      run[y + 1] = c;
-    }
-    for (int x = 0; x < m; x++) {
-      keys[i + x] = tile | (run[x] >> 32);
-      vals[i + x] = (uint32_t)run[x];
-    }
-  }
-  __syncthreads();
-  return red[4] == 0u;
-}
-
 // Per-tile bucket sorts in three size classes, each a persistent launch over
 // its class's tile list with shared memory sized for the class (so short
 // buckets run several CTAs per SM); the last class also takes the buckets
@@ -712,21 +536,20 @@ template <int NWARPS, int ITEMS>
 struct SegClass {
   static constexpr int THREADS = NWARPS * 32;
   static constexpr int CAP = NWARPS * 32 * ITEMS;
-  // two 32-bit ranking-key buffers, or the counters of the global-memory sort
-  static constexpr size_t KEYS_A = 2 * sizeof(uint32_t) * CAP;
-  static constexpr size_t KEYS_B = sizeof(uint32_t) * ((NWARPS + 1) * 256 + 8);
-  static constexpr size_t KEYS = ((KEYS_A > KEYS_B ? KEYS_A : KEYS_B) + 15) & ~(size_t)15;
-  static constexpr size_t SMEM = KEYS + RegSortSmem<NWARPS>::BYTES;
+  static constexpr size_t SMEM = 2 * sizeof(unsigned long long) * CAP + RegSortSmem<NWARPS>::BYTES;
+  static_assert(2 * sizeof(unsigned long long) * CAP >= sizeof(uint32_t) * ((NWARPS + 1) * 256 + 8),
+                "the oversized-bucket counters fit in the key buffers");
 };
 
 template <int NWARPS, int ITEMS, bool LAST>
-__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : (NWARPS == 8 ? 4 : 1)) k_tile_sort(const SegArgs A) {
+__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 2 : 1) k_tile_sort(const SegArgs A) {
   using C = SegClass<NWARPS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* sa = reinterpret_cast<uint32_t*>(smem);
-  uint32_t* sb = sa + C::CAP;
-  uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + C::KEYS);
-  uint32_t* tot = reinterpret_cast<uint32_t*>(smem + C::KEYS + ((RegSortSmem<NWARPS>::CNT_BYTES + 15) & ~(size_t)15));
+  unsigned long long* sa = reinterpret_cast<unsigned long long*>(smem);
+  unsigned long long* sb = sa + C::CAP;
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(sb + C::CAP);
+  uint32_t* tot = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(unsigned long long) * C::CAP +
+                                              ((RegSortSmem<NWARPS>::CNT_BYTES + 15) & ~(size_t)15));
   uint32_t* red = tot + 32;
   __shared__ uint32_t s_q;
   if (A.hdr->status != 0) return;
@@ -741,22 +564,19 @@ __global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : (NWARPS == 8 ?
     const uint2 rg = A.ranges[t];
     if (!s2d_check(rg.x <= rg.y && (int64_t)rg.y <= A.cap, A.hdr)) continue;
     const int n = (int)(rg.y - rg.x);
-    const uint64_t tile = (uint64_t)t << 32;
-    bool sorted = false;
-    if (!LAST || n <= C::CAP)
-      sorted = sort_bucket_reg32<NWARPS, ITEMS>(A.bucket + rg.x, n, sa, sb, cnt, tot, red, tile, A.keys + rg.x,
-                                                A.vals + rg.x);
-    if (!sorted) {
-      // longer than the class holds, or a run of equal depths longer than 64:
-      // the stable sort of the full composites in global memory
+    const unsigned long long* res;
+    if (!LAST || n <= C::CAP) {
+      res = sort_bucket_reg<NWARPS, ITEMS>(A.bucket + rg.x, n, sa, sb, cnt, tot, red);
+    } else {
       uint32_t* c32 = reinterpret_cast<uint32_t*>(smem);
       sort_bucket_any<NWARPS>(A.bucket + rg.x, A.scratch + rg.x, n, c32, c32 + (NWARPS + 1) * 256);
-      const unsigned long long* res = A.bucket + rg.x;
-      for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
-        const unsigned long long key = res[i];
-        A.keys[rg.x + i] = tile | (key >> 32);
-        A.vals[rg.x + i] = (uint32_t)key;
-      }
+      res = A.bucket + rg.x;
+    }
+    const uint64_t tile = (uint64_t)t << 32;
+    for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
+      const unsigned long long key = res[i];
+      A.keys[rg.x + i] = tile | (key >> 32);
+      A.vals[rg.x + i] = (uint32_t)key;
     }
     __syncthreads();
   }
