@@ -434,8 +434,6 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-maintenance", action="store_true", help="skip timing the map-maintenance kernels")
     ap.add_argument("--oracle-timing-child", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--spatial-order", action="store_true",
-                    help="store each 512x384 keyframe's surfels in 8x8 tile-blocked order (scenes.reorder_keyframes)")
     args = ap.parse_args()
     if args.oracle_timing_child:
         return oracle_timing_child()
@@ -463,9 +461,6 @@ def main():
     torch.cuda.set_device(dev)
 
     sc = make(multirank.submap_seed_offset(rank))  # each rank: its own independent submap
-    if args.spatial_order:
-        from paper_2604_03092_gb300 import scenes as _sc
-        sc = _sc.reorder_keyframes(sc, 512, 384)
     V = len(sc.views)
     params = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in
               (sc.means, sc.scales, sc.quats, sc.opacity, sc.rgb)]

@@ -507,27 +507,3 @@ def large_map_scene(seed: int = 4001, n_keyframes: int = 150, n_rooms: int = 6, 
                         n_rooms=n_rooms, step=0.12, deg=2.5, gains=gains, view_width=view_width,
                         view_height=view_height, view_f=view_f, n_views=n_views, with_targets=False)
 
-
-def tile_blocked_order(width: int, height: int, block: int = 8) -> np.ndarray:
-    """A permutation of one keyframe's per-pixel surfels (raster order)
-    into tile-blocked order: block rows, blocks left to right, raster order
-    inside a block, so that surfels of neighbouring pixels -- which cover the
-    same screen tiles from nearby views -- sit next to each other in memory."""
-    ys, xs = np.divmod(np.arange(width * height), width)
-    key = ((ys // block) * ((width + block - 1) // block) + xs // block) * (block * block) + (ys % block) * block + xs % block
-    return np.argsort(key, kind="stable")
-
-
-def reorder_keyframes(sc: Scene, width: int, height: int, block: int = 8) -> Scene:
-    """The scene with every keyframe's surfels (consecutive runs of
-    width * height, as the submap generators emit them) stored in
-    tile-blocked order; views render all surfels, so the images are those of
-    the original order up to the order of exactly equal depths."""
-    per = width * height
-    if sc.n % per:
-        raise ValueError("surfels are not whole keyframes of this size")
-    perm1 = tile_blocked_order(width, height, block)
-    perm = (np.arange(sc.n // per)[:, None] * per + perm1[None, :]).reshape(-1)
-    out = dataclasses.replace(sc, means=sc.means[perm], scales=sc.scales[perm], quats=sc.quats[perm],
-                              opacity=sc.opacity[perm], rgb=sc.rgb[perm])
-    return out
