@@ -920,25 +920,37 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         if constexpr (DIST) gz += dzd;
         if (P.depth_ray) pair_grads_ray_depth(e, qj, col.w, zp, w * u0.w + dzd, g, gz);
         if (kept) {
-          // zero terms (clamped alpha, low-pass pairs) skip their atomic
           float* sg = S.grad + j * SGRAD_STRIDE;
+          [[maybe_unused]] uint32_t outside = 0u;  // fixed point: terms outside the chunk's range
 #pragma unroll
           for (int q = 0; q < SGRAD_STRIDE; q++) {
             if (!want_n && q >= G_NX && q <= G_NZ) continue;  // no normal gradient requested
             const float t = q < 16 ? g[q] : gz;
             if constexpr (FIXED) {
-              // no scale yet (+inf) makes u infinite or NaN: the term goes outside
+              // no scale yet (+inf) makes u infinite or NaN: the term goes outside.
+              // Branch-free: a term outside this chunk's range adds zero here
+              // and is marked; the marked terms go to global memory below.
               const uint32_t w2 = gexp[q >> 1];
               const float u = t * __uint_as_float((q & 1) ? (w2 & 0xffff0000u) : (w2 << 16));
               const bool in = fabsf(u) < FIX_LIMIT;
-              if (in) atomicAdd(reinterpret_cast<int*>(sg + q), __float_as_int(__fadd_rn(u, FIX_MAGIC)) - FIX_MAGIC_BITS);
-              else if (t != 0.f) {  // outside this chunk's range (or not finite): add it exactly
-                atomicAdd(A.rgrad + (int64_t)S.idx[j] * GRAD_F + q, t);
+              atomicAdd(reinterpret_cast<int*>(sg + q),
+                        __float_as_int(__fadd_rn(in ? u : 0.f, FIX_MAGIC)) - FIX_MAGIC_BITS);
+              outside |= (!in && t != 0.f) ? (1u << q) : 0u;
+            } else {
+              if (t != 0.f) atomicAdd(sg + q, t);
+            }
+          }
+          if constexpr (FIXED) {
+            if (outside) {  // outside this chunk's range (or not finite): added exactly
+              float* dst = A.rgrad + (int64_t)S.idx[j] * GRAD_F;
+#pragma unroll
+              for (int q = 0; q < SGRAD_STRIDE; q++) {
+                if (!((outside >> q) & 1u)) continue;
+                const float t = q < 16 ? g[q] : gz;
+                atomicAdd(dst + q, t);
                 atomicMax(&S.ofl[q], (__float_as_uint(t) >> 23) & 0xffu);
                 n_outside++;
               }
-            } else {
-              if (t != 0.f) atomicAdd(sg + q, t);
             }
           }
         }
