@@ -389,36 +389,34 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           }
           const bool has = b != 0 && !done;
           if (!__any_sync(0xffffffffu, has)) break;
-          // Predicated: every lane evaluates a pair (an idle lane its word's
-          // first entry) and a pair that does not blend adds w = 0 to the
-          // finite accumulators, which leaves their bits unchanged.
-          const int j = wd * 32 + (has ? __ffs(b) - 1 : 0);
+          if (!has) continue;
+          const int j = wd * 32 + __ffs(b) - 1;
           b &= b - 1;
           Pair e;
           eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], px, py, P.lp_scale, P.alpha_max, e);
-          n_eval += has ? 1u : 0u;
+          n_eval++;
+          if (e.alpha < P.alpha_min) continue;
           const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
-          const bool pass = has && !(e.alpha < P.alpha_min);
-          const bool stop = Tn < P.t_min;
-          done = done || (pass && stop);
-          const bool blend = pass && !stop;
-          const float w = blend ? __fmul_rn(e.alpha, T) : 0.f;
+          if (Tn < P.t_min) {
+            done = true;
+            continue;
+          }
+          const float w = __fmul_rn(e.alpha, T);
           const float4 col = S.rec.col[j], nrm = S.rec.n[j];
           C0 = __fmaf_rn(w, col.x, C0);
           C1 = __fmaf_rn(w, col.y, C1);
           C2 = __fmaf_rn(w, col.z, C2);
           float zp = col.w;
           if (P.depth_ray) zp = pair_depth(e, col.w, S.rec.q[j].z, 1);
-          zp = blend ? zp : 0.f;
           if constexpr (DIST) Ds = __fmaf_rn(2.f * w, __fmaf_rn(zp, __fsub_rn(1.f, T), -D), Ds);
           D = __fmaf_rn(w, zp, D);
           N0 = __fmaf_rn(w, nrm.x, N0);
           N1 = __fmaf_rn(w, nrm.y, N1);
           N2 = __fmaf_rn(w, nrm.z, N2);
-          T = blend ? Tn : T;
-          last = blend ? (uint32_t)(base + j + 1) : last;
-          bl |= blend ? 1u << (j & 31) : 0u;
-          n_blend += blend ? 1u : 0u;
+          T = Tn;
+          last = (uint32_t)(base + j + 1);
+          bl |= 1u << (j & 31);
+          n_blend++;
         }
         S.bits[wid][wd][lane] = bl;
         for (int w2 = wd + 1; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;
