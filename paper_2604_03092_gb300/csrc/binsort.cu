@@ -487,32 +487,30 @@ __device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restr
   // that tie there form runs, put in (depth, surfel) order in place below
   const int lsb = max((int)dbits - 16, 0);
   unsigned long long* r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits - lsb, lsb);
-  auto top = [&](int i) -> uint32_t { return ((uint32_t)(r[i] >> 32) - dmin) >> lsb; };
+  // entries that tie on those bits form runs: each entry counts the keys of
+  // its run below its own (the composites are distinct) and lands at that
+  // rank in the other buffer, so every run is ordered in parallel; a run
+  // longer than 64 triggers one exact re-sort of the bucket instead
+  unsigned long long* o = r == sa ? sb : sa;
+  auto top = [&](unsigned long long x) -> uint32_t { return ((uint32_t)(x >> 32) - dmin) >> lsb; };
   for (int i = threadIdx.x; i < n; i += NT) {
-    const uint32_t d = top(i);
-    const bool starts = (i == 0 || top(i - 1) != d) && i + 1 < n && top(i + 1) == d;
-    if (!starts) continue;
-    int e = i + 1;
-    while (e + 1 < n && e - i < 64 && top(e + 1) == d) e++;
-    if (e + 1 < n && top(e + 1) == d) {
+    const unsigned long long key = r[i];
+    const uint32_t d = top(key);
+    int s = i, e = i;
+    while (s > 0 && i - s < 64 && top(r[s - 1]) == d) s--;
+    while (e + 1 < n && e - i < 64 && top(r[e + 1]) == d) e++;
+    if (e - s >= 64) {
       red[4] = 1u;
       continue;
     }
-    for (int x = i + 1; x <= e; x++) {
-      const unsigned long long key = r[x];
-      int y = x - 1;
-      while (y >= i && r[y] > key) {
-        r[y + 1] = r[y];
-        y--;
-      }
-      r[y + 1] = key;
-    }
+    int rank = 0;
+    for (int y = s; y <= e; y++) rank += r[y] < key ? 1 : 0;
+    o[s + rank] = key;
   }
   __syncthreads();
   if (red[4])
-    r = block_radix_reg<NWARPS, ITEMS>(r, r == sa ? sb : sa, n, cnt, tot, dmin, imin, (int)ibits,
-                                       (int)(dbits + ibits));
-  return r;
+    return block_radix_reg<NWARPS, ITEMS>(r, o, n, cnt, tot, dmin, imin, (int)ibits, (int)(dbits + ibits));
+  return o;
 }
 
 // Per-tile bucket sorts in three size classes, each a persistent launch over

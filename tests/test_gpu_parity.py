@@ -170,6 +170,39 @@ def test_bin_sort_long_buckets_and_equal_depths(n, tile):
     assert counts.max() > {2500: 1024, 9000: 4096, 30000: 12288}[n]
 
 
+def _tie_runs(keys):
+    """Lengths of the runs of sorted keys that share a bucket and the top 16
+    bits of their depth relative to the bucket's smallest (the bits the
+    bucket sort's radix passes take; longer ties are ordered afterwards)."""
+    tile = (keys >> np.uint64(32)).astype(np.int64)
+    z = (keys & np.uint64(0xffffffff)).astype(np.int64)
+    runs = []
+    for b in np.split(np.arange(len(keys)), np.flatnonzero(np.diff(tile)) + 1):
+        zz = z[b]
+        lsb = max(int(zz.max() - zz.min()).bit_length() - 16, 0)
+        top = (zz - zz.min()) >> lsb
+        runs.append(np.diff(np.r_[0, np.flatnonzero(np.diff(top)) + 1, len(top)]))
+    return np.concatenate(runs)
+
+
+@pytest.mark.parametrize("tile,spread", [((16, 16), 0.02), ((8, 8), 0.02), ((8, 8), 0.006)])
+def test_bin_sort_short_ties_on_the_radix_bits(tile, spread):
+    # half of the surfels lie within `spread` metres of depth 3 (distinct
+    # depths), the rest spread over 2..6: the runs tied on the radix bits are
+    # 2..64 long (up to 15 and 38 for the two spreads), so each is ordered by
+    # the per-run ranking, not by the exact re-sort
+    sc = scenes.random_scene(n=9000, width=64, height=48, f=60.0, seed=12, xy_range=0.3, scale_range=(0.2, 0.5),
+                             n_views=1, with_target=False)
+    sc.means[::2, 2] = np.float32(3.0) + np.random.default_rng(5).uniform(0.0, spread, sc.means[::2].shape[0]).astype(
+        np.float32)
+    _check_bin_sort(sc, tile)
+    okeys, _ = oracle.bin_sort([oracle.preprocess_scene_view(sc, 0, oracle_cfg(RasterConfig(tile_w=tile[0],
+                                                                                            tile_h=tile[1])))],
+                               [0], [(64 + tile[0] - 1) // tile[0]], [0])
+    runs = _tie_runs(okeys)
+    assert runs.max() <= 64 and (runs[runs > 1]).sum() > 2000, (runs.max(), (runs[runs > 1]).sum())
+
+
 # --------------------------------------------------------------------------
 # forward images
 # --------------------------------------------------------------------------
