@@ -159,7 +159,8 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->vals1 = take(sizeof(uint32_t) * L->cap);
   L->sort_hist = take(sizeof(uint32_t) * (256 * (size_t)L->sort_blocks + 256));
   L->ranges = take(sizeof(uint2) * T);
-  L->tile_count = take(sizeof(uint32_t) * T);
+  L->tile_count = take(sizeof(uint32_t) * T);   // instances per tile (counted by the preprocess)
+  L->tile_cursor = take(sizeof(uint32_t) * T);  // scatter cursors (from the tile scan)
   L->tile_order = take(sizeof(uint32_t) * T);
   L->tile_hist = take(sizeof(uint32_t) * (ORDER_BINS + 8));
   L->tile_class = take(sizeof(uint32_t) * 4 * (size_t)T);  // one list per bucket-sort size class

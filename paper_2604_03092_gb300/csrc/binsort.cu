@@ -41,19 +41,19 @@ struct TileBinArgs {
   int32_t V;
   int64_t R;
   int32_t tile_w, tile_h;
-  uint32_t* counts;  // per tile; the scan turns them into scatter cursors
+  uint32_t* cursors;  // per tile: the next free slot of its bucket (from the scan)
   unsigned long long* bucket;
-  int64_t cap;       // instance capacity (bucket length)
+  int64_t cap;        // instance capacity (bucket length)
   Header* hdr;
 };
 
-// Visit every (record, tile) instance; warp lanes hold consecutive records and
-// walk their tile rects in step so equal tiles can be aggregated.
-template <bool SCATTER>
-__global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
-  if (SCATTER && A.hdr->status != 0) return;
+// Scatter every (record, tile) instance into its tile's bucket; warp lanes
+// hold consecutive records and walk their tile rects in step, so runs of
+// equal tiles take one cursor atomic.  (The per-tile counts come from the
+// preprocess, which visits the same instances in the same way.)
+__global__ void __launch_bounds__(256) k_tile_scatter(const TileBinArgs A) {
+  if (A.hdr->status != 0) return;
   const int lane = threadIdx.x & 31;
-  const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // this thread's records only increase: follow the owning view forward
   int v = find_view_by_record(A.views, A.V, min64((int64_t)blockIdx.x * blockDim.x + threadIdx.x, A.R - 1));
@@ -78,25 +78,14 @@ __global__ void __launch_bounds__(256) k_tile_pass(const TileBinArgs A) {
     }
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
     for (uint32_t k = 0; k < kmax; k++) {
-      // neighbouring records (neighbouring pixels of a keyframe) mostly hit
-      // the same tile at the same k: lanes aggregate runs of equal tiles
       const bool has = k < nt;
-      const uint32_t t = has ? (uint32_t)(tbase + (ty0 + (int)k / w) * tilesx + tx0 + (int)k % w) : 0xffffffffu;
-      const uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1);
-      const uint32_t next = __shfl_down_sync(0xffffffffu, t, 1);
-      const uint32_t heads = __ballot_sync(0xffffffffu, has && (lane == 0 || prev != t));
-      const uint32_t ends = __ballot_sync(0xffffffffu, has && (lane == 31 || next != t));
-      const int leader = 31 - __clz(heads & (lt_mask | (1u << lane)));  // run start at or below this lane
-      const bool lead = has && leader == lane;
-      const uint32_t run = lead ? (uint32_t)(__ffs(ends & ~lt_mask) - lane) : 0u;
-      if (!SCATTER) {
-        if (lead) atomicAdd(A.counts + t, run);
-      } else {
-        uint32_t base = 0;
-        if (lead) base = atomicAdd(A.counts + t, run);
-        base = __shfl_sync(0xffffffffu, base, leader & 31);
-        if (has && s2d_check((int64_t)base + (lane - leader) < A.cap, A.hdr)) A.bucket[base + (uint32_t)(lane - leader)] = comp;
-      }
+      const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
+      const TileRun tr = tile_run(t, has, lane);
+      uint32_t base = 0;
+      if (tr.lead) base = atomicAdd(A.cursors + t, tr.run);
+      base = __shfl_sync(0xffffffffu, base, tr.leader & 31);
+      if (has && s2d_check((int64_t)base + (lane - tr.leader) < A.cap, A.hdr))
+        A.bucket[base + (uint32_t)(lane - tr.leader)] = comp;
     }
   }
 }
@@ -114,9 +103,11 @@ __device__ __forceinline__ int sort_class(uint32_t n) {
 
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
 // total and the capacity check; every non-empty tile is appended to the list
-// of its sort size class.
+// of its sort size class.  The counts are left as they are, so binning can
+// run again on the same preprocess.
 
-__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ counts, uint2* __restrict__ ranges,
+__global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ counts,
+                                                    uint32_t* __restrict__ cursors, uint2* __restrict__ ranges,
                                                     int64_t T, Header* __restrict__ hdr, int64_t cap,
                                                     uint32_t* __restrict__ class_list,
                                                     uint32_t* __restrict__ class_count) {
@@ -150,7 +141,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ count
     const bool fits = incl <= (unsigned long long)cap;
     if (i < T) {
       ranges[i] = fits ? make_uint2((uint32_t)start, (uint32_t)incl) : make_uint2(0u, 0u);
-      counts[i] = fits ? (uint32_t)start : 0u;
+      cursors[i] = fits ? (uint32_t)start : 0u;
     }
     // append the tile to its size class's list (order within a list is free)
     const int cls = (i < T && fits) ? sort_class((uint32_t)v) : -1;
@@ -450,17 +441,20 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
 }
 
 // Sort a bucket of at most NWARPS * 32 * ITEMS composites by (depth bits,
-// surfel index): load it from global memory into shared memory (finding the
+// surfel index) and write it out as (tile | depth bits) keys and surfel
+// values: load it from global memory into shared memory (finding the
 // bucket's depth and index ranges on the way), radix-sort the top 16 bits of
 // the depth relative to the smallest depth (two passes where the depths span
-// more), then put each run of entries that tie on those bits in (depth,
-// surfel) order in place by insertion (a run longer than 64 triggers one
-// exact re-sort on the relative composite key instead).  Returns the shared
-// buffer holding the result.
+// more), then write every entry out at its place: an entry that ties with no
+// neighbour on those bits at its sorted position, an entry of a run of ties
+// at the run's start plus the number of the run's composites below its own
+// (the composites are distinct), so every run is put in (depth, surfel)
+// order in parallel.  A run longer than 64 triggers one exact re-sort on the
+// relative composite key instead, whose result is written over.
 template <int NWARPS, int ITEMS>
-__device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restrict__ g, int n,
-                                               unsigned long long* sa, unsigned long long* sb, uint16_t* cnt,
-                                               uint32_t* tot, uint32_t* red) {
+__device__ void sort_bucket_reg(const unsigned long long* __restrict__ g, int n, unsigned long long* sa,
+                                unsigned long long* sb, uint16_t* cnt, uint32_t* tot, uint32_t* red,
+                                uint64_t tile, uint64_t* __restrict__ okeys, uint32_t* __restrict__ ovals) {
   constexpr int NT = NWARPS * 32;
   if (threadIdx.x == 0) {
     red[0] = 0xffffffffu; red[1] = 0u; red[2] = 0xffffffffu; red[3] = 0u; red[4] = 0u;
@@ -484,18 +478,30 @@ __device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restr
   const uint32_t dmin = red[0], dbits = (uint32_t)bits_of(red[1] - red[0]);
   const uint32_t imin = red[2], ibits = (uint32_t)bits_of(red[3] - red[2]);
   // radix passes over the top 16 bits of the relative depth only; entries
-  // that tie there form runs, put in (depth, surfel) order in place below
+  // that tie there form runs, put in (depth, surfel) order as they are
+  // written out below
   const int lsb = max((int)dbits - 16, 0);
   unsigned long long* r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits - lsb, lsb);
-  // entries that tie on those bits form runs: each entry counts the keys of
-  // its run below its own (the composites are distinct) and lands at that
-  // rank in the other buffer, so every run is ordered in parallel; a run
-  // longer than 64 triggers one exact re-sort of the bucket instead
-  unsigned long long* o = r == sa ? sb : sa;
+  const int lane = threadIdx.x & 31;
   auto top = [&](unsigned long long x) -> uint32_t { return ((uint32_t)(x >> 32) - dmin) >> lsb; };
-  for (int i = threadIdx.x; i < n; i += NT) {
-    const unsigned long long key = r[i];
+  auto emit = [&](int p, unsigned long long key) {
+    okeys[p] = tile | (key >> 32);
+    ovals[p] = (uint32_t)key;
+  };
+  for (int i0 = 0; i0 < n; i0 += NT) {
+    const int i = i0 + threadIdx.x;
+    const bool in = i < n;
+    const unsigned long long key = in ? r[i] : 0ull;
     const uint32_t d = top(key);
+    // the neighbours' top bits: the adjacent lanes' entries, across warps a load
+    uint32_t dp = __shfl_up_sync(0xffffffffu, d, 1), dn = __shfl_down_sync(0xffffffffu, d, 1);
+    if (lane == 0 && in && i > 0) dp = top(r[i - 1]);
+    if (lane == 31 && i + 1 < n) dn = top(r[i + 1]);
+    if (!in) continue;
+    if (!((i > 0 && dp == d) || (i + 1 < n && dn == d))) {
+      emit(i, key);
+      continue;
+    }
     int s = i, e = i;
     while (s > 0 && i - s < 64 && top(r[s - 1]) == d) s--;
     while (e + 1 < n && e - i < 64 && top(r[e + 1]) == d) e++;
@@ -505,12 +511,14 @@ __device__ unsigned long long* sort_bucket_reg(const unsigned long long* __restr
     }
     int rank = 0;
     for (int y = s; y <= e; y++) rank += r[y] < key ? 1 : 0;
-    o[s + rank] = key;
+    emit(s + rank, key);
   }
   __syncthreads();
-  if (red[4])
-    return block_radix_reg<NWARPS, ITEMS>(r, o, n, cnt, tot, dmin, imin, (int)ibits, (int)(dbits + ibits));
-  return o;
+  if (red[4]) {
+    const unsigned long long* x =
+        block_radix_reg<NWARPS, ITEMS>(r, r == sa ? sb : sa, n, cnt, tot, dmin, imin, (int)ibits, (int)(dbits + ibits));
+    for (int i = threadIdx.x; i < n; i += NT) emit(i, x[i]);
+  }
 }
 
 // Per-tile bucket sorts in three size classes, each a persistent launch over
@@ -562,19 +570,18 @@ __global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 2 : 1) k_tile_sort
     const uint2 rg = A.ranges[t];
     if (!s2d_check(rg.x <= rg.y && (int64_t)rg.y <= A.cap, A.hdr)) continue;
     const int n = (int)(rg.y - rg.x);
-    const unsigned long long* res;
+    const uint64_t tile = (uint64_t)t << 32;
     if (!LAST || n <= C::CAP) {
-      res = sort_bucket_reg<NWARPS, ITEMS>(A.bucket + rg.x, n, sa, sb, cnt, tot, red);
+      sort_bucket_reg<NWARPS, ITEMS>(A.bucket + rg.x, n, sa, sb, cnt, tot, red, tile, A.keys + rg.x, A.vals + rg.x);
     } else {
       uint32_t* c32 = reinterpret_cast<uint32_t*>(smem);
       sort_bucket_any<NWARPS>(A.bucket + rg.x, A.scratch + rg.x, n, c32, c32 + (NWARPS + 1) * 256);
-      res = A.bucket + rg.x;
-    }
-    const uint64_t tile = (uint64_t)t << 32;
-    for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
-      const unsigned long long key = res[i];
-      A.keys[rg.x + i] = tile | (key >> 32);
-      A.vals[rg.x + i] = (uint32_t)key;
+      const unsigned long long* res = A.bucket + rg.x;
+      for (int i = threadIdx.x; i < n; i += NWARPS * 32) {
+        const unsigned long long key = res[i];
+        A.keys[rg.x + i] = tile | (key >> 32);
+        A.vals[rg.x + i] = (uint32_t)key;
+      }
     }
     __syncthreads();
   }
@@ -598,10 +605,9 @@ static cudaError_t launch_tile_sort_class(const SegArgs& S, cudaStream_t st) {
 cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cudaStream_t st) {
   if (L.R <= 0 || L.T <= 0) return cudaSuccess;
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
-  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.tile_count);
+  const uint32_t* counts = reinterpret_cast<const uint32_t*>(ws + L.tile_count);  // written by the preprocess
+  uint32_t* cursors = reinterpret_cast<uint32_t*>(ws + L.tile_cursor);
   uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
-  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)L.T, st);
-  if (e != cudaSuccess) return e;
   TileBinArgs A;
   A.ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
   A.records = reinterpret_cast<const float4*>(ws + L.records);
@@ -610,20 +616,18 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   A.R = L.R;
   A.tile_w = P.tile_w;
   A.tile_h = P.tile_h;
-  A.counts = counts;
+  A.cursors = cursors;
   A.bucket = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   A.cap = L.cap;
   A.hdr = hdr;
   const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 16);
-  k_tile_pass<false><<<grid, 256, 0, st>>>(A);
-  count_launches(1);
   uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // per class: queue, list size
   uint32_t* class_list = reinterpret_cast<uint32_t*>(ws + L.tile_class);
-  e = cudaMemsetAsync(queues, 0, 2 * SORT_CLASSES * sizeof(uint32_t), st);
+  cudaError_t e = cudaMemsetAsync(queues, 0, 2 * SORT_CLASSES * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  k_tile_scan<<<1, 1024, 0, st>>>(counts, ranges, L.T, hdr, L.cap, class_list, queues + SORT_CLASSES);
+  k_tile_scan<<<1, 1024, 0, st>>>(counts, cursors, ranges, L.T, hdr, L.cap, class_list, queues + SORT_CLASSES);
   count_launches(1);
-  k_tile_pass<true><<<grid, 256, 0, st>>>(A);
+  k_tile_scatter<<<grid, 256, 0, st>>>(A);
   count_launches(1);
   SegArgs S;
   S.ranges = ranges;

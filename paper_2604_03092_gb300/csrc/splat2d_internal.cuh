@@ -89,7 +89,7 @@ constexpr float kLn2 = 0.69314718055994531f;
 // ---------------------------------------------------------------------------
 struct Layout {
   size_t header, views, groups, ntiles, records, rgrad, keys0, keys1, vals0, vals1, sort_hist, ranges,
-      tile_count, tile_order, tile_hist, tile_class, tfinal, last, dfinal, rcopy, bmask, total;
+      tile_count, tile_cursor, tile_order, tile_hist, tile_class, tfinal, last, dfinal, rcopy, bmask, total;
   int64_t bmask_words;  // 32-entry words of blended-pair masks (each holds one word per tile pixel)
   int64_t R, T, P, cap;
   int64_t n_work;     // sum over view groups of the surfel range sizes
@@ -245,6 +245,35 @@ __device__ __forceinline__ int find_group(const DGroup* groups, int G, int64_t w
     if (__ldg(&groups[mid].wbase) <= w) lo = mid; else hi = mid - 1;
   }
   return lo;
+}
+
+// Runs of equal tiles across the lanes of a full warp: each lane offers tile
+// t (has = false: none).  Neighbouring records (neighbouring pixels of a
+// keyframe) mostly hit the same tile at the same step, so one atomic per run
+// serves all its lanes.  `leader` is the lane starting the run that holds
+// this lane, `run` its length on the leader (0 elsewhere).
+struct TileRun {
+  int leader;
+  uint32_t run;
+  bool lead;
+};
+__device__ __forceinline__ TileRun tile_run(uint32_t t, bool has, int lane) {
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, t, 1);
+  const uint32_t next = __shfl_down_sync(0xffffffffu, t, 1);
+  const uint32_t heads = __ballot_sync(0xffffffffu, has && (lane == 0 || prev != t));
+  const uint32_t ends = __ballot_sync(0xffffffffu, has && (lane == 31 || next != t));
+  TileRun r;
+  r.leader = 31 - __clz(heads & (lt_mask | (1u << lane)));  // run start at or below this lane
+  r.lead = has && r.leader == lane;
+  r.run = r.lead ? (uint32_t)(__ffs(ends & ~lt_mask) - lane) : 0u;
+  return r;
+}
+
+// Global tile of the k-th tile (row-major) of a tile rect starting at tile
+// (tx0, ty0), w tiles wide, in a view whose tiles start at tbase.
+__device__ __forceinline__ uint32_t rect_tile(int tbase, int tilesx, int tx0, int ty0, int w, uint32_t k) {
+  return (uint32_t)(tbase + (ty0 + (int)k / w) * tilesx + tx0 + (int)k % w);
 }
 
 // Index checks of the checked build (compiled with S2D_CHECKS): a failed

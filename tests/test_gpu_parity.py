@@ -156,6 +156,27 @@ def test_bin_sort_matches_oracle_bit_exact(tile):
     _check_bin_sort(sc, tile)
 
 
+def test_bin_sort_runs_again_on_one_preprocess():
+    # the per-tile counts come from the preprocess and the binning leaves
+    # them as they are: a second binning gives the same lists and ranges
+    sc = scenes.random_scene(n=3000, width=100, height=70, f=70.0, seed=4, n_views=3)
+    rast, _, _ = gpu_forward(sc, RasterConfig(tile_w=16, tile_h=16))
+    lay = rast.layout
+    n = rast.stats()["n_instances"]
+
+    def snapshot():
+        return (rast.ws_tensor(lay.keys, n, torch.int64).cpu().numpy().copy(),
+                rast.ws_tensor(lay.vals, n, torch.int32).cpu().numpy().copy(),
+                rast.ws_tensor(lay.ranges, 2 * lay.n_tiles, torch.int32).cpu().numpy().copy())
+
+    first = snapshot()
+    rast.bin_sort()
+    torch.cuda.synchronize()
+    assert rast.stats()["n_instances"] == n
+    for a, b in zip(first, snapshot()):
+        assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("n,tile", [(2500, (16, 16)), (9000, (16, 16)), (30000, (16, 16)), (30000, (8, 8))])
 def test_bin_sort_long_buckets_and_equal_depths(n, tile):
     # every surfel covers the image centre, so the central tiles hold close to
