@@ -189,9 +189,8 @@ size_t splat2d_workspace_size(const splat2d_config* cfg, const splat2d_problem* 
  * transform, tangent frame from the normalised quaternion, the ray-splat
  * intersection transform, projected center, depth key, camera normal turned
  * to face the camera, culls, and the opacity-aware screen extent united with
- * the low-pass square, as a pixel rect.  Writes render records into `ws`,
- * counts the tiles of every visible pair into per-tile instance counts (the
- * first step of splat2d_bin_sort) and resets the device status.  Returns SPLAT2D_ERR_INVALID_ARG for a bad
+ * the low-pass square, as a pixel rect.  Writes render records into `ws` and
+ * resets the device status.  Returns SPLAT2D_ERR_INVALID_ARG for a bad
  * problem or surfel count mismatch, SPLAT2D_ERR_WORKSPACE_TOO_SMALL if
  * ws_bytes < splat2d_workspace_size().
  */
@@ -208,11 +207,11 @@ int splat2d_preprocess(const splat2d_config* cfg, const splat2d_problem* prob, c
  * value = surfel index, and the instances are put in key order, ties in
  * ascending surfel index (the order of a stable sort of the instances
  * emitted in surfel order).  The tile index is taken as the most significant
- * digit -- a scan of the per-tile counts splat2d_preprocess wrote gives each
- * tile's [start, end) range and a scatter fills per-tile buckets -- and each
- * bucket is then sorted by its depth bits with a radix sort in shared
- * memory.  Follows splat2d_preprocess on the same workspace (and may run
- * again on it: the counts are left unchanged).  If the instances exceed instance_capacity the
+ * digit -- a counting pass gives each tile's [start, end) range and a
+ * scatter fills per-tile buckets (both aggregate over a block of records in
+ * shared memory first, one global atomic per tile) -- and each bucket is
+ * then sorted by its depth bits with a radix sort in shared memory.  Follows splat2d_preprocess
+ * on the same workspace.  If the instances exceed instance_capacity the
  * device status becomes SPLAT2D_ERR_CAPACITY with the needed count and
  * every later kernel of the iteration does nothing; re-run with a larger
  * capacity.

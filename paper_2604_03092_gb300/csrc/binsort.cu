@@ -41,18 +41,36 @@ struct TileBinArgs {
   int32_t V;
   int64_t R;
   int32_t tile_w, tile_h;
-  uint32_t* cursors;  // per tile: the next free slot of its bucket (from the scan)
+  uint32_t* counts;   // per tile: instances (count pass) / next free bucket slot (scatter, from the scan)
   unsigned long long* bucket;
   int64_t cap;        // instance capacity (bucket length)
   Header* hdr;
 };
 
-// Scatter every (record, tile) instance into its tile's bucket; warp lanes
-// hold consecutive records and walk their tile rects in step, so runs of
-// equal tiles take one cursor atomic.  (The per-tile counts come from the
-// preprocess, which visits the same instances in the same way.)
-__global__ void __launch_bounds__(256) k_tile_scatter(const TileBinArgs A) {
-  if (A.hdr->status != 0) return;
+// Tile window of a CTA: the tiles [tmin, tmin + BIN_WIN) of the 256 records
+// it holds are counted in shared memory, then moved to global memory with
+// one atomic per tile.
+constexpr int BIN_WIN = 1024;
+// Instances k < BIN_KREG of a record keep their slot within the window's
+// run in registers between the scatter's count and write phases; the rest
+// (records over more than BIN_KREG tiles) take a global atomic each.
+constexpr int BIN_KREG = 8;
+
+// Visit every (record, tile) instance: the count pass adds them up per tile,
+// the scatter pass puts each record's composite (depth bits << 32 | surfel)
+// into its tiles' buckets.  A CTA holds 256 consecutive records (neighbouring
+// pixels of a keyframe, so neighbouring tiles of a view); warp lanes walk
+// their tile rects in step, and runs of lanes on one tile take one
+// shared-memory atomic on the CTA's tile window.  The window's nonzero
+// counts then take one global atomic per tile (the scatter's returns the
+// tile's block of bucket slots, and each instance lands at the block's start
+// plus its slot within the window).  Instances outside the window go to
+// global memory directly.
+template <bool SCATTER>
+__global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
+  __shared__ uint32_t win[BIN_WIN];
+  __shared__ uint32_t s_range[2];
+  if (SCATTER && A.hdr->status != 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // this thread's records only increase: follow the owning view forward
@@ -60,9 +78,9 @@ __global__ void __launch_bounds__(256) k_tile_scatter(const TileBinArgs A) {
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += stride) {
     const int64_t r = r0 + threadIdx.x;
     const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
-    if (!__any_sync(0xffffffffu, nt != 0)) continue;
     int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
     uint64_t comp = 0;
+    uint32_t tfirst = 0xffffffffu, tlast = 0u;
     if (nt) {
       while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
       const DView& vw = A.views[v];
@@ -70,23 +88,93 @@ __global__ void __launch_bounds__(256) k_tile_scatter(const TileBinArgs A) {
       const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
       tx0 = (int)(q0 & 0xffffu) / A.tile_w;
       ty0 = (int)(q0 >> 16) / A.tile_h;
-      const int tx1 = (int)(q1 & 0xffffu) / A.tile_w;
+      const int tx1 = (int)(q1 & 0xffffu) / A.tile_w, ty1 = (int)(q1 >> 16) / A.tile_h;
       w = tx1 - tx0 + 1;
       tbase = vw.tile_base;
       tilesx = vw.tiles_x;
       comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
+      tfirst = (uint32_t)(tbase + ty0 * tilesx + tx0);
+      tlast = (uint32_t)(tbase + ty1 * tilesx + tx1);
     }
+    if (threadIdx.x == 0) {
+      s_range[0] = 0xffffffffu;
+      s_range[1] = 0u;
+    }
+    for (int i = threadIdx.x; i < BIN_WIN; i += 256) win[i] = 0u;
+    __syncthreads();
+    const uint32_t wmin = __reduce_min_sync(0xffffffffu, tfirst), wmax = __reduce_max_sync(0xffffffffu, tlast);
+    if (lane == 0 && wmin <= wmax) {
+      atomicMin(&s_range[0], wmin);
+      atomicMax(&s_range[1], wmax);
+    }
+    __syncthreads();
+    const uint32_t tmin = s_range[0], tmax = s_range[1];
+    __syncthreads();  // the range is read before thread 0 resets it for the next records
+    if (tmin > tmax) continue;  // no instances in this CTA's records (uniform)
+    const uint32_t span = min(tmax - tmin + 1u, (uint32_t)BIN_WIN);
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
-    for (uint32_t k = 0; k < kmax; k++) {
+    // phase 1: window counts (the scatter keeps each instance's slot)
+    uint32_t slot[BIN_KREG];
+#pragma unroll
+    for (int k = 0; k < BIN_KREG; k++) {
+      slot[k] = 0u;
+      if ((uint32_t)k < kmax) {
+        const bool has = (uint32_t)k < nt;
+        const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, (uint32_t)k) : 0xffffffffu;
+        const bool in = has && t - tmin < span;
+        const TileRun tr = tile_run(in ? t : 0xffffffffu, in, lane);
+        uint32_t b = 0;
+        if (tr.lead) b = atomicAdd(&win[t - tmin], tr.run);
+        if (SCATTER) slot[k] = __shfl_sync(0xffffffffu, b, tr.leader & 31) + (uint32_t)(lane - tr.leader);
+        // outside the window: global atomics now
+        const TileRun to = tile_run(has && !in ? t : 0xffffffffu, has && !in, lane);
+        uint32_t g = 0;
+        if (to.lead) g = atomicAdd(A.counts + t, to.run);
+        if (SCATTER) {
+          g = __shfl_sync(0xffffffffu, g, to.leader & 31);
+          if (has && !in && s2d_check((int64_t)g + (lane - to.leader) < A.cap, A.hdr))
+            A.bucket[g + (uint32_t)(lane - to.leader)] = comp;
+        }
+      }
+    }
+    // the k >= BIN_KREG instances of large rects: global atomics
+    for (uint32_t k = BIN_KREG; k < kmax; k++) {
       const bool has = k < nt;
       const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
       const TileRun tr = tile_run(t, has, lane);
-      uint32_t base = 0;
-      if (tr.lead) base = atomicAdd(A.cursors + t, tr.run);
-      base = __shfl_sync(0xffffffffu, base, tr.leader & 31);
-      if (has && s2d_check((int64_t)base + (lane - tr.leader) < A.cap, A.hdr))
-        A.bucket[base + (uint32_t)(lane - tr.leader)] = comp;
+      uint32_t g = 0;
+      if (tr.lead) g = atomicAdd(A.counts + t, tr.run);
+      if (SCATTER) {
+        g = __shfl_sync(0xffffffffu, g, tr.leader & 31);
+        if (has && s2d_check((int64_t)g + (lane - tr.leader) < A.cap, A.hdr))
+          A.bucket[g + (uint32_t)(lane - tr.leader)] = comp;
+      }
     }
+    __syncthreads();
+    // phase 2: one global atomic per tile of the window (the scatter's
+    // returns the start of the tile's block of slots)
+    for (uint32_t i = threadIdx.x; i < span; i += 256) {
+      const uint32_t c = win[i];
+      if (c) {
+        const uint32_t g = atomicAdd(A.counts + tmin + i, c);
+        if (SCATTER) win[i] = g;
+      }
+    }
+    if (SCATTER) {
+      __syncthreads();
+      // phase 3: write the window's instances at their block start + slot
+#pragma unroll
+      for (int k = 0; k < BIN_KREG; k++) {
+        if ((uint32_t)k < nt) {
+          const uint32_t t = rect_tile(tbase, tilesx, tx0, ty0, w, (uint32_t)k);
+          if (t - tmin < span) {
+            const uint32_t at = win[t - tmin] + slot[k];
+            if (s2d_check((int64_t)at < A.cap, A.hdr)) A.bucket[at] = comp;
+          }
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -103,8 +191,7 @@ __device__ __forceinline__ int sort_class(uint32_t n) {
 
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
 // total and the capacity check; every non-empty tile is appended to the list
-// of its sort size class.  The counts are left as they are, so binning can
-// run again on the same preprocess.
+// of its sort size class.
 
 __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ counts,
                                                     uint32_t* __restrict__ cursors, uint2* __restrict__ ranges,
@@ -605,9 +692,11 @@ static cudaError_t launch_tile_sort_class(const SegArgs& S, cudaStream_t st) {
 cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cudaStream_t st) {
   if (L.R <= 0 || L.T <= 0) return cudaSuccess;
   Header* hdr = reinterpret_cast<Header*>(ws + L.header);
-  const uint32_t* counts = reinterpret_cast<const uint32_t*>(ws + L.tile_count);  // written by the preprocess
+  uint32_t* counts = reinterpret_cast<uint32_t*>(ws + L.tile_count);
   uint32_t* cursors = reinterpret_cast<uint32_t*>(ws + L.tile_cursor);
   uint2* ranges = reinterpret_cast<uint2*>(ws + L.ranges);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)L.T, st);
+  if (e != cudaSuccess) return e;
   TileBinArgs A;
   A.ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
   A.records = reinterpret_cast<const float4*>(ws + L.records);
@@ -616,18 +705,21 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   A.R = L.R;
   A.tile_w = P.tile_w;
   A.tile_h = P.tile_h;
-  A.cursors = cursors;
+  A.counts = counts;
   A.bucket = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   A.cap = L.cap;
   A.hdr = hdr;
-  const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 16);
+  const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 8);
+  k_tile_bin<false><<<grid, 256, 0, st>>>(A);
+  count_launches(1);
   uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // per class: queue, list size
   uint32_t* class_list = reinterpret_cast<uint32_t*>(ws + L.tile_class);
-  cudaError_t e = cudaMemsetAsync(queues, 0, 2 * SORT_CLASSES * sizeof(uint32_t), st);
+  e = cudaMemsetAsync(queues, 0, 2 * SORT_CLASSES * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   k_tile_scan<<<1, 1024, 0, st>>>(counts, cursors, ranges, L.T, hdr, L.cap, class_list, queues + SORT_CLASSES);
   count_launches(1);
-  k_tile_scatter<<<grid, 256, 0, st>>>(A);
+  A.counts = cursors;
+  k_tile_bin<true><<<grid, 256, 0, st>>>(A);
   count_launches(1);
   SegArgs S;
   S.ranges = ranges;

@@ -135,7 +135,6 @@ struct PreArgs {
   int64_t n_work;
   RastParams P;
   uint32_t* ntiles;
-  uint32_t* counts;  // instances per global tile (zeroed before the launch)
   float4* records;
   float4* rgrad;
   Header* hdr;
@@ -248,65 +247,30 @@ __device__ __forceinline__ uint32_t project_one(const PreArgs& A, const DView& v
   return ntx * nty;
 }
 
-// One thread per (surfel, view group) work item, looping over the group's
-// views.  The loops are warp-uniform (a lane past the end or past its
-// group's last view takes part with no pair), so after each view the warp
-// counts its pairs' tiles into the per-tile instance counts, one atomic per
-// run of lanes on the same tile.
 __global__ void __launch_bounds__(256, 3) k_preprocess(const PreArgs A) {
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   unsigned long long vis = 0;
-  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < A.n_work; w0 += stride) {
-    const int64_t w = w0 + lane;
-    const bool live = w < A.n_work;
-    int64_t s = 0;
-    int v0 = 0, v1 = 0;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < A.n_work; w += stride) {
+    const int g = find_group(A.groups, A.G, w);
+    const DGroup grp = A.groups[g];
+    const int64_t s = grp.soff + (w - grp.wbase);
     Surfel f;
-    float cr = 0.f, cg = 0.f, cb = 0.f;
-    if (live) {
-      const DGroup grp = A.groups[find_group(A.groups, A.G, w)];
-      s = grp.soff + (w - grp.wbase);
-      v0 = grp.v0;
-      v1 = grp.v1;
-      load_surfel(A.S, s, f);
-      cr = __ldg(A.S.rgb + 3 * s + 0);
-      cg = __ldg(A.S.rgb + 3 * s + 1);
-      cb = __ldg(A.S.rgb + 3 * s + 2);
-    }
-    const int nv = (int)__reduce_max_sync(0xffffffffu, (uint32_t)(v1 - v0));
-    for (int iv = 0; iv < nv; iv++) {
-      const int v = v0 + iv;
-      uint32_t nt = 0;
-      int tx0 = 0, ty0 = 0, tw = 1, tbase = 0, tilesx = 0;
-      if (v < v1) {
-        const DView& vw = A.views[v];
-        const int64_t rec = vw.rbase + (s - vw.soff);
-        float4 r[REC_F4];
-        nt = project_one(A, vw, f, r);
-        A.ntiles[rec] = nt;
-        if (nt) {
-          r[2].w = cr;
-          r[3].x = cg;
-          r[3].y = cb;
-          float4* dst = A.records + rec * REC_F4;
+    load_surfel(A.S, s, f);
+    const float cr = __ldg(A.S.rgb + 3 * s + 0), cg = __ldg(A.S.rgb + 3 * s + 1), cb = __ldg(A.S.rgb + 3 * s + 2);
+    for (int v = grp.v0; v < grp.v1; v++) {
+      const DView& vw = A.views[v];
+      const int64_t rec = vw.rbase + (s - vw.soff);
+      float4 r[REC_F4];
+      uint32_t nt = project_one(A, vw, f, r);
+      A.ntiles[rec] = nt;
+      if (nt) {
+        r[2].w = cr;
+        r[3].x = cg;
+        r[3].y = cb;
+        float4* dst = A.records + rec * REC_F4;
 #pragma unroll
-          for (int k = 0; k < REC_F4; k++) dst[k] = r[k];
-          vis++;
-          const uint32_t q0 = __float_as_uint(r[4].z), q1 = __float_as_uint(r[4].w);
-          tx0 = (int)(q0 & 0xffffu) / A.P.tile_w;
-          ty0 = (int)(q0 >> 16) / A.P.tile_h;
-          tw = (int)(q1 & 0xffffu) / A.P.tile_w - tx0 + 1;
-          tbase = vw.tile_base;
-          tilesx = vw.tiles_x;
-        }
-      }
-      const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
-      for (uint32_t k = 0; k < kmax; k++) {
-        const bool has = k < nt;
-        const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, tw, k) : 0xffffffffu;
-        const TileRun tr = tile_run(t, has, lane);
-        if (tr.lead) atomicAdd(A.counts + t, tr.run);
+        for (int k = 0; k < REC_F4; k++) dst[k] = r[k];
+        vis++;
       }
     }
   }
@@ -326,14 +290,9 @@ cudaError_t launch_preprocess(const splat2d_surfels* S, const Layout& L, const R
   A.n_work = n_work;
   A.P = P;
   A.ntiles = reinterpret_cast<uint32_t*>(ws + L.ntiles);
-  A.counts = reinterpret_cast<uint32_t*>(ws + L.tile_count);
   A.records = reinterpret_cast<float4*>(ws + L.records);
   A.rgrad = reinterpret_cast<float4*>(ws + L.rgrad);
   A.hdr = reinterpret_cast<Header*>(ws + L.header);
-  if (L.T > 0) {
-    const cudaError_t e = cudaMemsetAsync(A.counts, 0, sizeof(uint32_t) * (size_t)L.T, st);
-    if (e != cudaSuccess) return e;
-  }
   if (n_work <= 0) return cudaSuccess;
   int64_t blocks = (n_work + 255) / 256;
   int64_t cap = (int64_t)sm_count() * 16;

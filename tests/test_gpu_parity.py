@@ -157,8 +157,8 @@ def test_bin_sort_matches_oracle_bit_exact(tile):
 
 
 def test_bin_sort_runs_again_on_one_preprocess():
-    # the per-tile counts come from the preprocess and the binning leaves
-    # them as they are: a second binning gives the same lists and ranges
+    # binning depends only on the preprocess's records: a second binning on
+    # the same workspace gives the same lists and ranges
     sc = scenes.random_scene(n=3000, width=100, height=70, f=70.0, seed=4, n_views=3)
     rast, _, _ = gpu_forward(sc, RasterConfig(tile_w=16, tile_h=16))
     lay = rast.layout
