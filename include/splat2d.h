@@ -208,9 +208,8 @@ int splat2d_preprocess(const splat2d_config* cfg, const splat2d_problem* prob, c
  * ascending surfel index (the order of a stable sort of the instances
  * emitted in surfel order).  The tile index is taken as the most significant
  * digit -- a counting pass gives each tile's [start, end) range and a
- * scatter fills per-tile buckets (both aggregate over a block of records in
- * shared memory first, one global atomic per tile) -- and each bucket is
- * then sorted by its depth bits with a radix sort in shared memory.  Follows splat2d_preprocess
+ * scatter fills per-tile buckets -- and each bucket is then sorted by its
+ * depth bits with a radix sort in shared memory.  Follows splat2d_preprocess
  * on the same workspace.  If the instances exceed instance_capacity the
  * device status becomes SPLAT2D_ERR_CAPACITY with the needed count and
  * every later kernel of the iteration does nothing; re-run with a larger

@@ -47,134 +47,68 @@ struct TileBinArgs {
   Header* hdr;
 };
 
-// Tile window of a CTA: the tiles [tmin, tmin + BIN_WIN) of the 256 records
-// it holds are counted in shared memory, then moved to global memory with
-// one atomic per tile.
-constexpr int BIN_WIN = 1024;
-// Instances k < BIN_KREG of a record keep their slot within the window's
-// run in registers between the scatter's count and write phases; the rest
-// (records over more than BIN_KREG tiles) take a global atomic each.
-constexpr int BIN_KREG = 8;
+// Records a thread takes per iteration of the tile passes: their loads are
+// issued together, so a thread waits on one round of DRAM latency per
+// BIN_ILP records instead of per record (the passes are latency-bound: each
+// record is a count load and then, if it is visible, its rect).
+constexpr int BIN_ILP = 4;
 
 // Visit every (record, tile) instance: the count pass adds them up per tile,
 // the scatter pass puts each record's composite (depth bits << 32 | surfel)
-// into its tiles' buckets.  A CTA holds 256 consecutive records (neighbouring
-// pixels of a keyframe, so neighbouring tiles of a view); warp lanes walk
-// their tile rects in step, and runs of lanes on one tile take one
-// shared-memory atomic on the CTA's tile window.  The window's nonzero
-// counts then take one global atomic per tile (the scatter's returns the
-// tile's block of bucket slots, and each instance lands at the block's start
-// plus its slot within the window).  Instances outside the window go to
-// global memory directly.
+// into its tiles' buckets.  Warp lanes hold consecutive records (neighbouring
+// pixels of a keyframe) and walk their tile rects in step, so runs of lanes
+// on one tile take one atomic.
 template <bool SCATTER>
 __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
-  __shared__ uint32_t win[BIN_WIN];
-  __shared__ uint32_t s_range[2];
   if (SCATTER && A.hdr->status != 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // this thread's records only increase: follow the owning view forward
   int v = find_view_by_record(A.views, A.V, min64((int64_t)blockIdx.x * blockDim.x + threadIdx.x, A.R - 1));
-  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += stride) {
-    const int64_t r = r0 + threadIdx.x;
-    const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
-    int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
-    uint64_t comp = 0;
-    uint32_t tfirst = 0xffffffffu, tlast = 0u;
-    if (nt) {
-      while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
-      const DView& vw = A.views[v];
-      const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
-      const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
-      tx0 = (int)(q0 & 0xffffu) / A.tile_w;
-      ty0 = (int)(q0 >> 16) / A.tile_h;
-      const int tx1 = (int)(q1 & 0xffffu) / A.tile_w, ty1 = (int)(q1 >> 16) / A.tile_h;
-      w = tx1 - tx0 + 1;
-      tbase = vw.tile_base;
-      tilesx = vw.tiles_x;
-      comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
-      tfirst = (uint32_t)(tbase + ty0 * tilesx + tx0);
-      tlast = (uint32_t)(tbase + ty1 * tilesx + tx1);
-    }
-    if (threadIdx.x == 0) {
-      s_range[0] = 0xffffffffu;
-      s_range[1] = 0u;
-    }
-    for (int i = threadIdx.x; i < BIN_WIN; i += 256) win[i] = 0u;
-    __syncthreads();
-    const uint32_t wmin = __reduce_min_sync(0xffffffffu, tfirst), wmax = __reduce_max_sync(0xffffffffu, tlast);
-    if (lane == 0 && wmin <= wmax) {
-      atomicMin(&s_range[0], wmin);
-      atomicMax(&s_range[1], wmax);
-    }
-    __syncthreads();
-    const uint32_t tmin = s_range[0], tmax = s_range[1];
-    __syncthreads();  // the range is read before thread 0 resets it for the next records
-    if (tmin > tmax) continue;  // no instances in this CTA's records (uniform)
-    const uint32_t span = min(tmax - tmin + 1u, (uint32_t)BIN_WIN);
-    const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
-    // phase 1: window counts (the scatter keeps each instance's slot)
-    uint32_t slot[BIN_KREG];
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += BIN_ILP * stride) {
+    uint32_t nt[BIN_ILP];
+    float4 f4[BIN_ILP];
 #pragma unroll
-    for (int k = 0; k < BIN_KREG; k++) {
-      slot[k] = 0u;
-      if ((uint32_t)k < kmax) {
-        const bool has = (uint32_t)k < nt;
-        const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, (uint32_t)k) : 0xffffffffu;
-        const bool in = has && t - tmin < span;
-        const TileRun tr = tile_run(in ? t : 0xffffffffu, in, lane);
-        uint32_t b = 0;
-        if (tr.lead) b = atomicAdd(&win[t - tmin], tr.run);
-        if (SCATTER) slot[k] = __shfl_sync(0xffffffffu, b, tr.leader & 31) + (uint32_t)(lane - tr.leader);
-        // outside the window: global atomics now
-        const TileRun to = tile_run(has && !in ? t : 0xffffffffu, has && !in, lane);
-        uint32_t g = 0;
-        if (to.lead) g = atomicAdd(A.counts + t, to.run);
+    for (int j = 0; j < BIN_ILP; j++) {
+      const int64_t r = r0 + j * stride + threadIdx.x;
+      nt[j] = r < A.R ? __ldg(A.ntiles + r) : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < BIN_ILP; j++) {
+      const int64_t r = r0 + j * stride + threadIdx.x;
+      f4[j] = nt[j] ? __ldg(A.records + r * REC_F4 + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < BIN_ILP; j++) {
+      if (!__any_sync(0xffffffffu, nt[j] != 0)) continue;
+      const int64_t r = r0 + j * stride + threadIdx.x;
+      int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
+      uint64_t comp = 0;
+      if (nt[j]) {
+        while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
+        const DView& vw = A.views[v];
+        const uint32_t q0 = __float_as_uint(f4[j].z), q1 = __float_as_uint(f4[j].w);
+        tx0 = (int)(q0 & 0xffffu) / A.tile_w;
+        ty0 = (int)(q0 >> 16) / A.tile_h;
+        w = (int)(q1 & 0xffffu) / A.tile_w - tx0 + 1;
+        tbase = vw.tile_base;
+        tilesx = vw.tiles_x;
+        comp = ((uint64_t)__float_as_uint(f4[j].y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
+      }
+      const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt[j]);
+      for (uint32_t k = 0; k < kmax; k++) {
+        const bool has = k < nt[j];
+        const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
+        const TileRun tr = tile_run(t, has, lane);
+        uint32_t base = 0;
+        if (tr.lead) base = atomicAdd(A.counts + t, tr.run);
         if (SCATTER) {
-          g = __shfl_sync(0xffffffffu, g, to.leader & 31);
-          if (has && !in && s2d_check((int64_t)g + (lane - to.leader) < A.cap, A.hdr))
-            A.bucket[g + (uint32_t)(lane - to.leader)] = comp;
+          base = __shfl_sync(0xffffffffu, base, tr.leader & 31);
+          if (has && s2d_check((int64_t)base + (lane - tr.leader) < A.cap, A.hdr))
+            A.bucket[base + (uint32_t)(lane - tr.leader)] = comp;
         }
       }
     }
-    // the k >= BIN_KREG instances of large rects: global atomics
-    for (uint32_t k = BIN_KREG; k < kmax; k++) {
-      const bool has = k < nt;
-      const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
-      const TileRun tr = tile_run(t, has, lane);
-      uint32_t g = 0;
-      if (tr.lead) g = atomicAdd(A.counts + t, tr.run);
-      if (SCATTER) {
-        g = __shfl_sync(0xffffffffu, g, tr.leader & 31);
-        if (has && s2d_check((int64_t)g + (lane - tr.leader) < A.cap, A.hdr))
-          A.bucket[g + (uint32_t)(lane - tr.leader)] = comp;
-      }
-    }
-    __syncthreads();
-    // phase 2: one global atomic per tile of the window (the scatter's
-    // returns the start of the tile's block of slots)
-    for (uint32_t i = threadIdx.x; i < span; i += 256) {
-      const uint32_t c = win[i];
-      if (c) {
-        const uint32_t g = atomicAdd(A.counts + tmin + i, c);
-        if (SCATTER) win[i] = g;
-      }
-    }
-    if (SCATTER) {
-      __syncthreads();
-      // phase 3: write the window's instances at their block start + slot
-#pragma unroll
-      for (int k = 0; k < BIN_KREG; k++) {
-        if ((uint32_t)k < nt) {
-          const uint32_t t = rect_tile(tbase, tilesx, tx0, ty0, w, (uint32_t)k);
-          if (t - tmin < span) {
-            const uint32_t at = win[t - tmin] + slot[k];
-            if (s2d_check((int64_t)at < A.cap, A.hdr)) A.bucket[at] = comp;
-          }
-        }
-      }
-    }
-    __syncthreads();
   }
 }
 
@@ -709,8 +643,17 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   A.bucket = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   A.cap = L.cap;
   A.hdr = hdr;
-  const int grid = (int)min64((L.R + 255) / 256, (int64_t)sm_count() * 8);
-  k_tile_bin<false><<<grid, 256, 0, st>>>(A);
+  // one wave of resident CTAs (each walks its records BIN_ILP at a time)
+  static int per_sm[2] = {-1, -1};
+  for (int s = 0; s < 2; s++)
+    if (per_sm[s] < 0) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[s], s ? k_tile_bin<true> : k_tile_bin<false>, 256, 0);
+      if (per_sm[s] < 1) per_sm[s] = 1;
+    }
+  const int64_t blocks = (L.R + 255) / 256;
+  const int grid0 = (int)min64(blocks, (int64_t)sm_count() * per_sm[0]);
+  const int grid1 = (int)min64(blocks, (int64_t)sm_count() * per_sm[1]);
+  k_tile_bin<false><<<grid0, 256, 0, st>>>(A);
   count_launches(1);
   uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // per class: queue, list size
   uint32_t* class_list = reinterpret_cast<uint32_t*>(ws + L.tile_class);
@@ -719,7 +662,7 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   k_tile_scan<<<1, 1024, 0, st>>>(counts, cursors, ranges, L.T, hdr, L.cap, class_list, queues + SORT_CLASSES);
   count_launches(1);
   A.counts = cursors;
-  k_tile_bin<true><<<grid, 256, 0, st>>>(A);
+  k_tile_bin<true><<<grid1, 256, 0, st>>>(A);
   count_launches(1);
   SegArgs S;
   S.ranges = ranges;
