@@ -47,12 +47,6 @@ struct TileBinArgs {
   Header* hdr;
 };
 
-// Records a thread takes per iteration of the tile passes: their loads are
-// issued together, so a thread waits on one round of DRAM latency per
-// BIN_ILP records instead of per record (the passes are latency-bound: each
-// record is a count load and then, if it is visible, its rect).
-constexpr int BIN_ILP = 4;
-
 // Visit every (record, tile) instance: the count pass adds them up per tile,
 // the scatter pass puts each record's composite (depth bits << 32 | surfel)
 // into its tiles' buckets.  Warp lanes hold consecutive records (neighbouring
@@ -65,48 +59,35 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // this thread's records only increase: follow the owning view forward
   int v = find_view_by_record(A.views, A.V, min64((int64_t)blockIdx.x * blockDim.x + threadIdx.x, A.R - 1));
-  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += BIN_ILP * stride) {
-    uint32_t nt[BIN_ILP];
-    float4 f4[BIN_ILP];
-#pragma unroll
-    for (int j = 0; j < BIN_ILP; j++) {
-      const int64_t r = r0 + j * stride + threadIdx.x;
-      nt[j] = r < A.R ? __ldg(A.ntiles + r) : 0u;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += stride) {
+    const int64_t r = r0 + threadIdx.x;
+    const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
+    if (!__any_sync(0xffffffffu, nt != 0)) continue;
+    int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
+    uint64_t comp = 0;
+    if (nt) {
+      while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
+      const DView& vw = A.views[v];
+      const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
+      const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
+      tx0 = (int)(q0 & 0xffffu) / A.tile_w;
+      ty0 = (int)(q0 >> 16) / A.tile_h;
+      w = (int)(q1 & 0xffffu) / A.tile_w - tx0 + 1;
+      tbase = vw.tile_base;
+      tilesx = vw.tiles_x;
+      comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
     }
-#pragma unroll
-    for (int j = 0; j < BIN_ILP; j++) {
-      const int64_t r = r0 + j * stride + threadIdx.x;
-      f4[j] = nt[j] ? __ldg(A.records + r * REC_F4 + 4) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int j = 0; j < BIN_ILP; j++) {
-      if (!__any_sync(0xffffffffu, nt[j] != 0)) continue;
-      const int64_t r = r0 + j * stride + threadIdx.x;
-      int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
-      uint64_t comp = 0;
-      if (nt[j]) {
-        while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
-        const DView& vw = A.views[v];
-        const uint32_t q0 = __float_as_uint(f4[j].z), q1 = __float_as_uint(f4[j].w);
-        tx0 = (int)(q0 & 0xffffu) / A.tile_w;
-        ty0 = (int)(q0 >> 16) / A.tile_h;
-        w = (int)(q1 & 0xffffu) / A.tile_w - tx0 + 1;
-        tbase = vw.tile_base;
-        tilesx = vw.tiles_x;
-        comp = ((uint64_t)__float_as_uint(f4[j].y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
-      }
-      const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt[j]);
-      for (uint32_t k = 0; k < kmax; k++) {
-        const bool has = k < nt[j];
-        const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
-        const TileRun tr = tile_run(t, has, lane);
-        uint32_t base = 0;
-        if (tr.lead) base = atomicAdd(A.counts + t, tr.run);
-        if (SCATTER) {
-          base = __shfl_sync(0xffffffffu, base, tr.leader & 31);
-          if (has && s2d_check((int64_t)base + (lane - tr.leader) < A.cap, A.hdr))
-            A.bucket[base + (uint32_t)(lane - tr.leader)] = comp;
-        }
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
+    for (uint32_t k = 0; k < kmax; k++) {
+      const bool has = k < nt;
+      const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
+      const TileRun tr = tile_run(t, has, lane);
+      uint32_t base = 0;
+      if (tr.lead) base = atomicAdd(A.counts + t, tr.run);
+      if (SCATTER) {
+        base = __shfl_sync(0xffffffffu, base, tr.leader & 31);
+        if (has && s2d_check((int64_t)base + (lane - tr.leader) < A.cap, A.hdr))
+          A.bucket[base + (uint32_t)(lane - tr.leader)] = comp;
       }
     }
   }
@@ -643,16 +624,8 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   A.bucket = reinterpret_cast<unsigned long long*>(ws + L.keys1);
   A.cap = L.cap;
   A.hdr = hdr;
-  // one wave of resident CTAs (each walks its records BIN_ILP at a time)
-  static int per_sm[2] = {-1, -1};
-  for (int s = 0; s < 2; s++)
-    if (per_sm[s] < 0) {
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[s], s ? k_tile_bin<true> : k_tile_bin<false>, 256, 0);
-      if (per_sm[s] < 1) per_sm[s] = 1;
-    }
   const int64_t blocks = (L.R + 255) / 256;
-  const int grid0 = (int)min64(blocks, (int64_t)sm_count() * per_sm[0]);
-  const int grid1 = (int)min64(blocks, (int64_t)sm_count() * per_sm[1]);
+  const int grid0 = (int)min64(blocks, (int64_t)sm_count() * 16), grid1 = grid0;
   k_tile_bin<false><<<grid0, 256, 0, st>>>(A);
   count_launches(1);
   uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.tile_hist) + ORDER_BINS;  // per class: queue, list size
