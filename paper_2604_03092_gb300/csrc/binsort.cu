@@ -63,25 +63,27 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
     const int64_t r = r0 + threadIdx.x;
     const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
     if (!__any_sync(0xffffffffu, nt != 0)) continue;
-    int tx0 = 0, ty0 = 0, w = 1, tbase = 0, tilesx = 0;
+    // the rect's tiles in row-major order: t walks a row, then jumps to the
+    // next row's first tile (no division per step)
+    uint32_t t = 0, wrap = 0;
+    int left = 0, w = 1;
     uint64_t comp = 0;
     if (nt) {
       while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
       const DView& vw = A.views[v];
       const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
       const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
-      tx0 = (int)(q0 & 0xffffu) / A.tile_w;
-      ty0 = (int)(q0 >> 16) / A.tile_h;
+      const int tx0 = (int)(q0 & 0xffffu) / A.tile_w, ty0 = (int)(q0 >> 16) / A.tile_h;
       w = (int)(q1 & 0xffffu) / A.tile_w - tx0 + 1;
-      tbase = vw.tile_base;
-      tilesx = vw.tiles_x;
+      t = (uint32_t)(vw.tile_base + ty0 * vw.tiles_x + tx0);
+      wrap = (uint32_t)(vw.tiles_x - w + 1);
+      left = w;
       comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
     }
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
-    for (uint32_t k = 0; k < kmax; k++) {
+    for (uint32_t k = 0; k < kmax; k++, t += (--left == 0) ? wrap : 1u, left = left == 0 ? w : left) {
       const bool has = k < nt;
-      const uint32_t t = has ? rect_tile(tbase, tilesx, tx0, ty0, w, k) : 0xffffffffu;
-      const TileRun tr = tile_run(t, has, lane);
+      const TileRun tr = tile_run(has ? t : 0xffffffffu, has, lane);
       uint32_t base = 0;
       if (tr.lead) base = atomicAdd(A.counts + t, tr.run);
       if (SCATTER) {

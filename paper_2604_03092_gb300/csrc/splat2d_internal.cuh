@@ -270,12 +270,6 @@ __device__ __forceinline__ TileRun tile_run(uint32_t t, bool has, int lane) {
   return r;
 }
 
-// Global tile of the k-th tile (row-major) of a tile rect starting at tile
-// (tx0, ty0), w tiles wide, in a view whose tiles start at tbase.
-__device__ __forceinline__ uint32_t rect_tile(int tbase, int tilesx, int tx0, int ty0, int w, uint32_t k) {
-  return (uint32_t)(tbase + (ty0 + (int)k / w) * tilesx + tx0 + (int)k % w);
-}
-
 // Index checks of the checked build (compiled with S2D_CHECKS): a failed
 // check records SPLAT2D_ERR_BOUNDS in the status word (unless an earlier
 // status is there) and the caller skips the access; nothing traps.  In the
