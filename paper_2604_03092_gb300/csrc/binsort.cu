@@ -52,6 +52,9 @@ struct TileBinArgs {
 // into its tiles' buckets.  Warp lanes hold consecutive records (neighbouring
 // pixels of a keyframe) and walk their tile rects in step, so runs of lanes
 // on one tile take one atomic.
+// Steps of the scatter whose cursor atomics are in flight together.
+constexpr int BIN_KB = 4;
+
 template <bool SCATTER>
 __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
   if (SCATTER && A.hdr->status != 0) return;
@@ -81,15 +84,41 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
       comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
     }
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
-    for (uint32_t k = 0; k < kmax; k++, t += (--left == 0) ? wrap : 1u, left = left == 0 ? w : left) {
-      const bool has = k < nt;
-      const TileRun tr = tile_run(has ? t : 0xffffffffu, has, lane);
-      uint32_t base = 0;
-      if (tr.lead) base = atomicAdd(A.counts + t, tr.run);
-      if (SCATTER) {
-        base = __shfl_sync(0xffffffffu, base, tr.leader & 31);
-        if (has && s2d_check((int64_t)base + (lane - tr.leader) < A.cap, A.hdr))
-          A.bucket[base + (uint32_t)(lane - tr.leader)] = comp;
+    auto advance = [&]() {
+      t += (--left == 0) ? wrap : 1u;
+      left = left == 0 ? w : left;
+    };
+    if (!SCATTER) {
+      for (uint32_t k = 0; k < kmax; k++, advance()) {
+        const bool has = k < nt;
+        const TileRun tr = tile_run(has ? t : 0xffffffffu, has, lane);
+        if (tr.lead) atomicAdd(A.counts + t, tr.run);
+      }
+    } else {
+      // the cursor atomics of BIN_KB steps are issued before any of their
+      // results is used, so the warp waits on one L2 round trip per batch
+      for (uint32_t k0 = 0; k0 < kmax; k0 += BIN_KB) {
+        uint32_t base[BIN_KB];
+        int leader[BIN_KB];
+#pragma unroll
+        for (int j = 0; j < BIN_KB; j++) {
+          base[j] = 0u;
+          leader[j] = -1;
+          if (k0 + j < kmax) {
+            const bool has = k0 + j < nt;
+            const TileRun tr = tile_run(has ? t : 0xffffffffu, has, lane);
+            if (tr.lead) base[j] = atomicAdd(A.counts + t, tr.run);
+            leader[j] = has ? tr.leader : -1;
+            advance();
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < BIN_KB; j++) {
+          if (k0 + j >= kmax) break;  // uniform across the warp
+          const uint32_t b = __shfl_sync(0xffffffffu, base[j], leader[j] & 31);
+          if (leader[j] >= 0 && s2d_check((int64_t)b + (lane - leader[j]) < A.cap, A.hdr))
+            A.bucket[b + (uint32_t)(lane - leader[j])] = comp;
+        }
       }
     }
   }
