@@ -173,7 +173,8 @@ void splat2d_default_config(splat2d_config* cfg);
 
 /* Bytes of workspace the problem needs (0 if the arguments are invalid).
  * The workspace holds, per (view, surfel) pair of every view's range, an
- * 80-byte render record, an 80-byte gradient record and a 4-byte tile count;
+ * 80-byte render record, an 80-byte gradient record, a 4-byte tile count
+ * and a 16-byte binning entry (depth key, pixel rect, tile count);
  * per unit of instance_capacity, 24 bytes of sort keys and values, an 80-byte
  * sorted-order record copy and tile_w * tile_h / 8 bytes of blended-pair
  * masks; and 12 bytes per pixel. */

@@ -151,6 +151,7 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->views = take(sizeof(DView) * V);
   L->groups = take(sizeof(DGroup) * G);
   L->ntiles = take(sizeof(uint32_t) * R);
+  L->bins = take(sizeof(uint4) * R);  // per record: depth bits, rect (2 words), tile count
   L->records = take(sizeof(float4) * REC_F4 * R);
   L->rgrad = take(sizeof(float) * GRAD_F * R);
   L->keys0 = take(sizeof(uint64_t) * L->cap);

@@ -35,8 +35,8 @@ namespace s2d {
 // order with ties in surfel order -- the stable sort of the instance keys.
 // ---------------------------------------------------------------------------
 struct TileBinArgs {
-  const uint32_t* ntiles;
-  const float4* records;
+  const uint4* bins;  // per record: depth bits, rect x0 | y0 << 16, rect x1 | y1 << 16, tile count
+
   const DView* views;
   int32_t V;
   int64_t R;
@@ -64,7 +64,10 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
   int v = find_view_by_record(A.views, A.V, min64((int64_t)blockIdx.x * blockDim.x + threadIdx.x, A.R - 1));
   for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < A.R; r0 += stride) {
     const int64_t r = r0 + threadIdx.x;
-    const uint32_t nt = r < A.R ? __ldg(A.ntiles + r) : 0u;
+    // 16 contiguous bytes per record (the records themselves are 80 bytes
+    // apart: reading their rects pulled most of each record from DRAM)
+    const uint4 e = r < A.R ? __ldg(A.bins + r) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t nt = e.w;
     if (!__any_sync(0xffffffffu, nt != 0)) continue;
     // the rect's tiles in row-major order: t walks a row, then jumps to the
     // next row's first tile (no division per step)
@@ -74,14 +77,13 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
     if (nt) {
       while (v + 1 < A.V && __ldg(&A.views[v + 1].rbase) <= r) v++;
       const DView& vw = A.views[v];
-      const float4 f4 = __ldg(A.records + r * REC_F4 + 4);
-      const uint32_t q0 = __float_as_uint(f4.z), q1 = __float_as_uint(f4.w);
+      const uint32_t q0 = e.y, q1 = e.z;
       const int tx0 = (int)(q0 & 0xffffu) / A.tile_w, ty0 = (int)(q0 >> 16) / A.tile_h;
       w = (int)(q1 & 0xffffu) / A.tile_w - tx0 + 1;
       t = (uint32_t)(vw.tile_base + ty0 * vw.tiles_x + tx0);
       wrap = (uint32_t)(vw.tiles_x - w + 1);
       left = w;
-      comp = ((uint64_t)__float_as_uint(f4.y) << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
+      comp = ((uint64_t)e.x << 32) | (uint64_t)(uint32_t)(vw.soff + (r - vw.rbase));
     }
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, nt);
     auto advance = [&]() {
@@ -644,8 +646,7 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)L.T, st);
   if (e != cudaSuccess) return e;
   TileBinArgs A;
-  A.ntiles = reinterpret_cast<const uint32_t*>(ws + L.ntiles);
-  A.records = reinterpret_cast<const float4*>(ws + L.records);
+  A.bins = reinterpret_cast<const uint4*>(ws + L.bins);
   A.views = reinterpret_cast<const DView*>(ws + L.views);
   A.V = L.V;
   A.R = L.R;

@@ -135,6 +135,7 @@ struct PreArgs {
   int64_t n_work;
   RastParams P;
   uint32_t* ntiles;
+  uint4* bins;  // per record: the binning passes' 16 bytes (depth bits, rect, tile count)
   float4* records;
   float4* rgrad;
   Header* hdr;
@@ -263,6 +264,8 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const PreArgs A) {
       float4 r[REC_F4];
       uint32_t nt = project_one(A, vw, f, r);
       A.ntiles[rec] = nt;
+      A.bins[rec] = nt ? make_uint4(__float_as_uint(r[4].y), __float_as_uint(r[4].z), __float_as_uint(r[4].w), nt)
+                       : make_uint4(0u, 0u, 0u, 0u);
       if (nt) {
         r[2].w = cr;
         r[3].x = cg;
@@ -290,6 +293,7 @@ cudaError_t launch_preprocess(const splat2d_surfels* S, const Layout& L, const R
   A.n_work = n_work;
   A.P = P;
   A.ntiles = reinterpret_cast<uint32_t*>(ws + L.ntiles);
+  A.bins = reinterpret_cast<uint4*>(ws + L.bins);
   A.records = reinterpret_cast<float4*>(ws + L.records);
   A.rgrad = reinterpret_cast<float4*>(ws + L.rgrad);
   A.hdr = reinterpret_cast<Header*>(ws + L.header);

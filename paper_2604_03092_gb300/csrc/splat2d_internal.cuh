@@ -88,7 +88,7 @@ constexpr float kLn2 = 0.69314718055994531f;
 // Workspace layout (identical on every call for the same problem)
 // ---------------------------------------------------------------------------
 struct Layout {
-  size_t header, views, groups, ntiles, records, rgrad, keys0, keys1, vals0, vals1, sort_hist, ranges,
+  size_t header, views, groups, ntiles, bins, records, rgrad, keys0, keys1, vals0, vals1, sort_hist, ranges,
       tile_count, tile_cursor, tile_order, tile_hist, tile_class, tfinal, last, dfinal, rcopy, bmask, total;
   int64_t bmask_words;  // 32-entry words of blended-pair masks (each holds one word per tile pixel)
   int64_t R, T, P, cap;
