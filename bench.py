@@ -752,8 +752,8 @@ def main():
     n_pix = rast.n_pixels
     pe_f, pe_b = st["fwd_pairs_evaluated"], st["bwd_pairs_evaluated"]
     work = {  # stage: (bytes, FP32 lane-instructions, MUFU ops)
-        "preprocess": (56 * rast.n_surfels + 4 * lay.n_records + 80 * n_vis, 0, 0),
-        "bin_sort": (8 * lay.n_records + 32 * n_vis + 8 * n_inst + 20 * n_inst, 0, 0),
+        "preprocess": (56 * rast.n_surfels + 20 * lay.n_records + 80 * n_vis, 0, 0),
+        "bin_sort": (32 * lay.n_records + 8 * n_inst + 20 * n_inst, 0, 0),
         "render_fwd": (FWD_BYTES_INST * n_inst + FWD_BYTES_PIX * n_pix, INSTR_FWD * pe_f, MUFU_FWD * pe_f),
         "render_bwd": (BWD_BYTES_INST * n_inst + BWD_BYTES_PIX * n_pix + BWD_BYTES_VIS * n_vis,
                        INSTR_BWD * pe_b, MUFU_BWD * pe_b),
