@@ -150,9 +150,6 @@ struct RenderArgs {
 // also to the sorted-order copy the backward reads.  (An L2 prefetch of the
 // next chunk's records issued here cost the forward 0.56 ms on the submap:
 // the gather's requests compete with it.)
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw, int th,
                                             int64_t base, int count, SRecs<CHUNK>& s_rec, bool keep_copy) {
@@ -167,23 +164,19 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
 }
 
 // Copies entries [base, base + count) from the sorted-order record copy the
-// forward left (contiguous, so the loads coalesce and wait on nothing), the
-// record index of each entry (for the gradient records) from the list, and
-// asks L2 for the contiguous records of the chunk processed next.
+// forward left (contiguous, so the loads coalesce and wait on nothing) and
+// the record index of each entry (for the gradient records) from the list.
+// (An L2 prefetch of the next chunk's records made no measurable difference.)
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw,
                                                 int th, int64_t base, int count, SRecs<CHUNK>& s_rec,
-                                                uint32_t* s_idx, int64_t nbase, int ncount) {
+                                                uint32_t* s_idx) {
   for (int j = threadIdx.x; j < count; j += NT) {
     const uint32_t s = __ldg(A.vals + base + j);
     if (!s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) continue;
     unpack_record<CHUNK>(A.rcopy + (base + j) * REC_F4, s_rec, j, tx0, ty0, tw, th);
     s_idx[j] = (uint32_t)(vw.rbase + ((int64_t)s - vw.soff));
   }
-  // 128-byte lines of the next chunk's records
-  const int64_t b0 = (nbase * REC_F4 * 16) >> 7, b1 = ((nbase + ncount) * REC_F4 * 16 + 127) >> 7;
-  const char* c0 = reinterpret_cast<const char*>(A.rcopy);
-  for (int64_t l = b0 + threadIdx.x; ncount > 0 && l < b1; l += NT) prefetch_l2(c0 + (l << 7));
 }
 
 // Per-lane visit masks.  Each warp owns an 8x4 pixel patch (lane = column
@@ -760,8 +753,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int count = (int)(min64(hi, (int64_t)top) - lo);
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
-      const int64_t nlo = max64((int64_t)range.x, lo - CHUNK);  // the chunk in front, processed next
-      stage_chunk_seq<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, S.idx, nlo, (int)(lo - nlo));
+      stage_chunk_seq<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, S.idx);
       // per-pixel masks of this chunk: the entries the forward blended at the pixel
       {
         const int64_t w0 = woff + ((lo - (int64_t)range.x) >> 5);
