@@ -373,7 +373,7 @@ struct RegSortSmem {
 template <int NWARPS, int ITEMS>
 __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned long long* b, int n, uint16_t* cnt,
                                                uint32_t* tot, uint32_t dmin, uint32_t imin, int ishift, int nbits,
-                                               int lsb = 0, const unsigned long long* pre = nullptr) {
+                                               int lsb = 0) {
   constexpr int NT = NWARPS * 32, CP = RegSortSmem<NWARPS>::CP;
   static_assert(NWARPS % 8 == 0, "the counter scan takes 8 counters per thread");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -388,20 +388,10 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
     const int shift = 8 * pass;
     unsigned long long key[ITEMS];
     uint32_t off[ITEMS];
-    // the first pass may take its keys from `pre` (this warp's slice in
-    // global memory, the bucket itself) instead of from shared memory
-    if (pass == 0 && pre) {
 #pragma unroll
-      for (int k = 0; k < ITEMS; k++) {
-        const int i = lo + k * 32 + lane;
-        key[k] = (k < nr && i < hi) ? __ldg(pre + i) : 0ull;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < ITEMS; k++) {
-        const int i = lo + k * 32 + lane;
-        key[k] = (k < nr && i < hi) ? src[i] : 0ull;
-      }
+    for (int k = 0; k < ITEMS; k++) {
+      const int i = lo + k * 32 + lane;
+      key[k] = (k < nr && i < hi) ? src[i] : 0ull;
     }
     for (int i = threadIdx.x; i < 256 * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
     __syncthreads();
@@ -505,11 +495,10 @@ __device__ void sort_bucket_reg(const unsigned long long* __restrict__ g, int n,
     red[0] = 0xffffffffu; red[1] = 0u; red[2] = 0xffffffffu; red[3] = 0u; red[4] = 0u;
   }
   __syncthreads();
-  // the bucket's depth and index ranges (the bucket is read again, from L2,
-  // by the first radix pass: no shared-memory copy of it is made here)
   uint32_t dmn = 0xffffffffu, dmx = 0u, imn = 0xffffffffu, imx = 0u;
   for (int i = threadIdx.x; i < n; i += NT) {
     const unsigned long long x = g[i];
+    sa[i] = x;
     const uint32_t d = (uint32_t)(x >> 32), s = (uint32_t)x;
     dmn = min(dmn, d); dmx = max(dmx, d); imn = min(imn, s); imx = max(imx, s);
   }
@@ -527,13 +516,7 @@ __device__ void sort_bucket_reg(const unsigned long long* __restrict__ g, int n,
   // that tie there form runs, put in (depth, surfel) order as they are
   // written out below
   const int lsb = max((int)dbits - 16, 0);
-  unsigned long long* r = sa;
-  if (dbits == 0) {  // one depth: no radix pass, the bucket goes to shared memory as it is
-    for (int i = threadIdx.x; i < n; i += NT) sa[i] = g[i];
-    __syncthreads();
-  } else {
-    r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits - lsb, lsb, g);
-  }
+  unsigned long long* r = block_radix_reg<NWARPS, ITEMS>(sa, sb, n, cnt, tot, dmin, 0u, -1, (int)dbits - lsb, lsb);
   const int lane = threadIdx.x & 31;
   auto top = [&](unsigned long long x) -> uint32_t { return ((uint32_t)(x >> 32) - dmin) >> lsb; };
   auto emit = [&](int p, unsigned long long key) {
