@@ -150,11 +150,31 @@ struct RenderArgs {
 // also to the sorted-order copy the backward reads.  (An L2 prefetch of the
 // next chunk's records issued here cost the forward 0.56 ms on the submap:
 // the gather's requests compete with it.)
+// The list entries come in `ent`: entry threadIdx.x + e * NT of the chunk in
+// ent[e], read a chunk ahead (see load_entries), so the record loads issue
+// without first waiting on the list.
+template <int NT, int CHUNK>
+__host__ __device__ constexpr int entries_per_thread() {
+  return (CHUNK + NT - 1) / NT;
+}
+template <int NT, int CHUNK>
+__device__ __forceinline__ void load_entries(const RenderArgs& A, int64_t base, int64_t end,
+                                             uint32_t (&ent)[entries_per_thread<NT, CHUNK>()]) {
+#pragma unroll
+  for (int e = 0; e < entries_per_thread<NT, CHUNK>(); e++) {
+    const int j = (int)threadIdx.x + e * NT;
+    ent[e] = (j < CHUNK && base + j < end) ? __ldg(A.vals + base + j) : 0u;
+  }
+}
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw, int th,
-                                            int64_t base, int count, SRecs<CHUNK>& s_rec, bool keep_copy) {
-  for (int j = threadIdx.x; j < count; j += NT) {
-    const uint32_t s = __ldg(A.vals + base + j);
+                                            int64_t base, int count, SRecs<CHUNK>& s_rec, bool keep_copy,
+                                            const uint32_t (&ent)[entries_per_thread<NT, CHUNK>()]) {
+#pragma unroll
+  for (int e = 0; e < entries_per_thread<NT, CHUNK>(); e++) {
+    const int j = (int)threadIdx.x + e * NT;
+    if (j >= count) break;
+    const uint32_t s = ent[e];
     if (s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) {
       const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
       unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j, tx0, ty0, tw, th,
@@ -333,6 +353,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
     float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f, Ds = 0.f;
     uint32_t last = range.x;
     bool done = !inside;
+    // list entries of the chunk staged next, read one chunk ahead
+    uint32_t ent[entries_per_thread<NT, CHUNK>()];
+    load_entries<NT, CHUNK>(A, range.x, range.y, ent);
     for (int64_t base = range.x; base < range.y; base += CHUNK) {
       const int n_act = __syncthreads_count(!done);
       if (n_act == 0) break;
@@ -346,7 +369,13 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         S.nact = 0;
         S.next = 0;
       }
-      stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, base, count, S.rec, true);
+      {
+        uint32_t cur[entries_per_thread<NT, CHUNK>()];
+#pragma unroll
+        for (int e = 0; e < entries_per_thread<NT, CHUNK>(); e++) cur[e] = ent[e];
+        load_entries<NT, CHUNK>(A, base + CHUNK, range.y, ent);
+        stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, base, count, S.rec, true, cur);
+      }
       __syncthreads();
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
