@@ -52,6 +52,13 @@ INSTR_FWD, MUFU_FWD = 32, 2
 INSTR_BWD, MUFU_BWD = 100, 3
 FWD_BYTES_INST, FWD_BYTES_PIX = 80, 40
 BWD_BYTES_INST, BWD_BYTES_PIX, BWD_BYTES_VIS = 80, 72, 80
+# the same figures as reported with the roofline's kernel ("pair" = processed pair)
+PER_UNIT = {
+    "render_fwd": {"instr_per_pair": INSTR_FWD, "mufu_per_pair": MUFU_FWD, "bytes_per_instance": FWD_BYTES_INST,
+                   "bytes_per_pixel": FWD_BYTES_PIX},
+    "render_bwd": {"instr_per_pair": INSTR_BWD, "mufu_per_pair": MUFU_BWD, "bytes_per_instance": BWD_BYTES_INST,
+                   "bytes_per_pixel": BWD_BYTES_PIX, "bytes_per_visible": BWD_BYTES_VIS},
+}
 
 # The same kernels' own FP32 arithmetic per pair, counted from their source
 # (an FMA counts 2), reported beside the figures above:
@@ -791,9 +798,7 @@ def main():
                                 f" lanes x {clk_hz / 1e6:.0f} MHz")}
     roof["work"] = {"bytes": d["bytes"], "lane_instr": d["lane_instr"], "mufu": d["mufu"],
                     "frac_hbm": d["frac_hbm"], "frac_alu": d["frac_alu"], "sm_count": n_sm,
-                    "per_unit": ({"instr_per_pair": INSTR_BWD, "mufu_per_pair": MUFU_BWD,
-                                  "bytes_per_instance": BWD_BYTES_INST, "bytes_per_pixel": BWD_BYTES_PIX,
-                                  "bytes_per_visible": BWD_BYTES_VIS} if dom == "render_bwd" else None)}
+                    "per_unit": PER_UNIT.get(dom)}
 
     # ---- CPU baseline (the oracle, host cores, bounded sample) -----------------
     cpu = None
