@@ -384,6 +384,11 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
   const int passes = (nbits + 7) >> 3;
   unsigned long long* src = a;
   unsigned long long* dst = b;
+  // counters start at zero: each warp clears its own (digit, warp) column;
+  // the last user of the array (a scan that reads every column) finished
+  // behind a block barrier
+  for (int d = lane; d < 256; d += 32) cnt[d * CP + wid] = 0;
+  __syncwarp();
   for (int pass = 0; pass < passes; pass++) {
     const int shift = 8 * pass;
     unsigned long long key[ITEMS];
@@ -393,8 +398,6 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
       const int i = lo + k * 32 + lane;
       key[k] = (k < nr && i < hi) ? src[i] : 0ull;
     }
-    for (int i = threadIdx.x; i < 256 * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
-    __syncthreads();
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
       if (k < nr) {
@@ -442,17 +445,11 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
       }
       if (lane == 31) tot[wid] = x;
       __syncthreads();
-      if (wid == 0) {
-        uint32_t y = lane < NWARPS ? tot[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-          if (lane >= o) y += z;
-        }
-        if (lane < NWARPS) tot[lane] = y;
-      }
-      __syncthreads();
-      uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
+      // the warps in front: each warp adds up their totals itself (a
+      // broadcast read each), which saves a barrier over a scan by one warp
+      uint32_t before = 0;
+      for (int w = 0; w < wid; w++) before += tot[w];
+      uint32_t ex = x - sum + before;
 #pragma unroll
       for (int j = 0; j < 8; j++) {
         cnt[d * CP + w0 + j] = (uint16_t)ex;
@@ -467,6 +464,11 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
         dst[(uint32_t)cnt[d * CP + wid] + (off[k] & 0xffffu)] = key[k];
       }
     }
+    // the next pass's counters: a warp's ranking and scatter touch only its
+    // own column, so each warp clears its column itself (no block barrier)
+    __syncwarp();
+    for (int d = lane; d < 256; d += 32) cnt[d * CP + wid] = 0;
+    __syncwarp();
     __syncthreads();
     unsigned long long* t = src;
     src = dst;
