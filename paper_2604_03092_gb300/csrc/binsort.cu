@@ -445,11 +445,17 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
       }
       if (lane == 31) tot[wid] = x;
       __syncthreads();
-      // the warps in front: each warp adds up their totals itself (a
-      // broadcast read each), which saves a barrier over a scan by one warp
-      uint32_t before = 0;
-      for (int w = 0; w < wid; w++) before += tot[w];
-      uint32_t ex = x - sum + before;
+      if (wid == 0) {
+        uint32_t y = lane < NWARPS ? tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+          if (lane >= o) y += z;
+        }
+        if (lane < NWARPS) tot[lane] = y;
+      }
+      __syncthreads();
+      uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
 #pragma unroll
       for (int j = 0; j < 8; j++) {
         cnt[d * CP + w0 + j] = (uint16_t)ex;
