@@ -384,11 +384,6 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
   const int passes = (nbits + 7) >> 3;
   unsigned long long* src = a;
   unsigned long long* dst = b;
-  // counters start at zero: each warp clears its own (digit, warp) column;
-  // the last user of the array (a scan that reads every column) finished
-  // behind a block barrier
-  for (int d = lane; d < 256; d += 32) cnt[d * CP + wid] = 0;
-  __syncwarp();
   for (int pass = 0; pass < passes; pass++) {
     const int shift = 8 * pass;
     unsigned long long key[ITEMS];
@@ -398,6 +393,8 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
       const int i = lo + k * 32 + lane;
       key[k] = (k < nr && i < hi) ? src[i] : 0ull;
     }
+    for (int i = threadIdx.x; i < 256 * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
       if (k < nr) {
@@ -470,11 +467,6 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
         dst[(uint32_t)cnt[d * CP + wid] + (off[k] & 0xffffu)] = key[k];
       }
     }
-    // the next pass's counters: a warp's ranking and scatter touch only its
-    // own column, so each warp clears its column itself (no block barrier)
-    __syncwarp();
-    for (int d = lane; d < 256; d += 32) cnt[d * CP + wid] = 0;
-    __syncwarp();
     __syncthreads();
     unsigned long long* t = src;
     src = dst;
