@@ -37,7 +37,6 @@ struct SRecs {
   float4 col[CHUNK];  // r g b z
   float4 n[CHUNK];    // nx ny nz, and in .w the pixel rect clipped to the tile (see pack_tile_rect)
 };
-static_assert(sizeof(SRecs<64>) == 5 * 64 * sizeof(float4), "five float4 arrays, no padding: the record copy's layout");
 
 // A record's pixel rect clipped to the tile and made relative to its origin,
 // one byte per bound: x0 | y0 << 8 | x1 << 16 | y1 << 24 (inclusive; an
@@ -52,9 +51,16 @@ __device__ __forceinline__ uint32_t pack_tile_rect(int x0, int y0, int x1, int y
 
 template <int CHUNK>
 __device__ __forceinline__ void unpack_record(const float4* __restrict__ rec, SRecs<CHUNK>& o, int j, int tx0,
-                                              int ty0, int tw, int th) {
+                                              int ty0, int tw, int th, float4* __restrict__ copy = nullptr) {
   const float4 f0 = __ldg(rec + 0), f1 = __ldg(rec + 1), f2 = __ldg(rec + 2), f3 = __ldg(rec + 3),
                f4 = __ldg(rec + 4);
+  if (copy) {  // streaming stores: read back only by the backward, long after
+    __stcs(copy + 0, f0);
+    __stcs(copy + 1, f1);
+    __stcs(copy + 2, f2);
+    __stcs(copy + 3, f3);
+    __stcs(copy + 4, f4);
+  }
   const float2 lo = unpack_half2_scaled(__float_as_uint(f0.z));
   o.c[j] = make_float4(f0.x, f0.y, lo.x, lo.y);
   o.p[j] = f1;
@@ -140,7 +146,8 @@ struct RenderArgs {
 };
 
 // Copies entries [base, base + count) of the sorted list's records to shared
-// memory (a dependent gather: list entry, then record).  (An L2 prefetch of the
+// memory (a dependent gather: list entry, then record), and with keep_copy
+// also to the sorted-order copy the backward reads.  (An L2 prefetch of the
 // next chunk's records issued here cost the forward 0.56 ms on the submap:
 // the gather's requests compete with it.)
 // The list entries come in `ent`: entry threadIdx.x + e * NT of the chunk in
@@ -161,7 +168,7 @@ __device__ __forceinline__ void load_entries(const RenderArgs& A, int64_t base, 
 }
 template <int NT, int CHUNK>
 __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw, int th,
-                                            int64_t base, int count, SRecs<CHUNK>& s_rec,
+                                            int64_t base, int count, SRecs<CHUNK>& s_rec, bool keep_copy,
                                             const uint32_t (&ent)[entries_per_thread<NT, CHUNK>()]) {
 #pragma unroll
   for (int e = 0; e < entries_per_thread<NT, CHUNK>(); e++) {
@@ -170,37 +177,24 @@ __device__ __forceinline__ void stage_chunk(const RenderArgs& A, const DView& vw
     const uint32_t s = ent[e];
     if (s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) {
       const int64_t rec = vw.rbase + ((int64_t)s - vw.soff);
-      unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j, tx0, ty0, tw, th);
+      unpack_record<CHUNK>(A.records + rec * REC_F4, s_rec, j, tx0, ty0, tw, th,
+                           keep_copy ? A.rcopy + (base + j) * REC_F4 : nullptr);
     }
   }
 }
 
-// The sorted-order record copy holds, per instance i, its staged entry as the
-// forward's shared arrays hold it (c, p, q, col, n: five float4, the rect
-// already clipped to the tile), at rcopy + i * REC_F4.
-// The forward writes chunk [base, base + count) of it from shared memory,
-// thread k taking float4 k, k + NT, ... of the chunk's 5 * count, so each
-// warp's stores cover 512 contiguous bytes.
-template <int NT, int CHUNK>
-__device__ __forceinline__ void write_copy(const RenderArgs& A, int64_t base, int count, const SRecs<CHUNK>& s_rec) {
-  const float4* f = reinterpret_cast<const float4*>(&s_rec);
-  float4* dst = A.rcopy + base * REC_F4;
-  for (int i = threadIdx.x; i < count * REC_F4; i += NT) __stcs(dst + i, f[(i % REC_F4) * CHUNK + i / REC_F4]);
-}
 // Copies entries [base, base + count) from the sorted-order record copy the
-// forward left (contiguous, already in shared-memory form: the loads
-// coalesce and nothing is unpacked) and the record index of each entry (for
-// the gradient records) from the list.  (An L2 prefetch of the next chunk's
-// records made no measurable difference.)
+// forward left (contiguous, so the loads coalesce and wait on nothing) and
+// the record index of each entry (for the gradient records) from the list.
+// (An L2 prefetch of the next chunk's records made no measurable difference.)
 template <int NT, int CHUNK>
-__device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView& vw, int64_t base, int count,
-                                                SRecs<CHUNK>& s_rec, uint32_t* s_idx) {
-  float4* f = reinterpret_cast<float4*>(&s_rec);
-  const float4* src = A.rcopy + base * REC_F4;
-  for (int i = threadIdx.x; i < count * REC_F4; i += NT) f[(i % REC_F4) * CHUNK + i / REC_F4] = __ldcs(src + i);
+__device__ __forceinline__ void stage_chunk_seq(const RenderArgs& A, const DView& vw, int tx0, int ty0, int tw,
+                                                int th, int64_t base, int count, SRecs<CHUNK>& s_rec,
+                                                uint32_t* s_idx) {
   for (int j = threadIdx.x; j < count; j += NT) {
     const uint32_t s = __ldg(A.vals + base + j);
     if (!s2d_check((int64_t)s >= vw.soff && (int64_t)s < vw.soff + vw.scnt, A.hdr)) continue;
+    unpack_record<CHUNK>(A.rcopy + (base + j) * REC_F4, s_rec, j, tx0, ty0, tw, th);
     s_idx[j] = (uint32_t)(vw.rbase + ((int64_t)s - vw.soff));
   }
 }
@@ -380,10 +374,9 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
 #pragma unroll
         for (int e = 0; e < entries_per_thread<NT, CHUNK>(); e++) cur[e] = ent[e];
         load_entries<NT, CHUNK>(A, base + CHUNK, range.y, ent);
-        stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, base, count, S.rec, cur);
+        stage_chunk<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, base, count, S.rec, true, cur);
       }
       __syncthreads();
-      write_copy<NT, CHUNK>(A, base, count, S.rec);  // read back by the backward, long after
       if (n_act > P.fwd_tail * NW) {
         // ---- bulk: each lane walks its own pixel's entries --------------------
         if (__all_sync(0xffffffffu, done)) {
@@ -789,7 +782,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
       const int count = (int)(min64(hi, (int64_t)top) - lo);
       const int nwd = (count + 31) >> 5;
       const bool act = inside && (int64_t)my_last > lo;
-      stage_chunk_seq<NT, CHUNK>(A, vw, lo, count, S.rec, S.idx);
+      stage_chunk_seq<NT, CHUNK>(A, vw, tx0, ty0, TW, TH, lo, count, S.rec, S.idx);
       // per-pixel masks of this chunk: the entries the forward blended at the pixel
       {
         const int64_t w0 = woff + ((lo - (int64_t)range.x) >> 5);
