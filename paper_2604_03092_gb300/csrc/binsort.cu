@@ -384,7 +384,63 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
   const int passes = (nbits + 7) >> 3;
   unsigned long long* src = a;
   unsigned long long* dst = b;
-  for (int pass = 0; pass < passes; pass++) {
+  auto digit = [&](unsigned long long key, int shift) -> uint32_t {
+    const unsigned long long dk = (unsigned long long)((uint32_t)(key >> 32) - dmin);
+    const unsigned long long kk = ishift < 0 ? dk : ((dk << ishift) | (unsigned long long)((uint32_t)key - imin));
+    return (uint32_t)(kk >> (shift + lsb)) & 0xffu;
+  };
+  int first = 0;
+  if (passes > 0) {
+    // The first pass may leave equal digits in any order (the order it starts
+    // from is arbitrary anyway): each key takes its slot within its digit from
+    // one shared atomic on a 256-bin histogram, and only the 256 bins are
+    // scanned.  The later passes keep the order of equal digits (below).
+    uint32_t* hist = reinterpret_cast<uint32_t*>(cnt);  // 256 words of the counter space
+    unsigned long long key[ITEMS];
+    uint32_t off[ITEMS];
+    for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0u;
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+      const int i = lo + k * 32 + lane;
+      key[k] = (k < nr && i < hi) ? src[i] : 0ull;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+      if (k < nr && lo + k * 32 + lane < hi) {
+        const uint32_t d = digit(key[k], 0);
+        off[k] = (d << 16) | atomicAdd(&hist[d], 1u);
+      }
+    }
+    __syncthreads();
+    uint32_t v = 0, x = 0;
+    if (threadIdx.x < 256) {
+      v = hist[threadIdx.x];
+      x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) tot[wid] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t before = 0;
+      for (int w = 0; w < wid; w++) before += tot[w];
+      hist[threadIdx.x] = before + x - v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++)
+      if (k < nr && lo + k * 32 + lane < hi) dst[hist[off[k] >> 16] + (off[k] & 0xffffu)] = key[k];
+    __syncthreads();
+    unsigned long long* t = src;
+    src = dst;
+    dst = t;
+    first = 1;
+  }
+  for (int pass = first; pass < passes; pass++) {
     const int shift = 8 * pass;
     unsigned long long key[ITEMS];
     uint32_t off[ITEMS];
@@ -399,13 +455,7 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
     for (int k = 0; k < ITEMS; k++) {
       if (k < nr) {
         const bool valid = lo + k * 32 + lane < hi;
-        uint32_t d = 0;
-        if (valid) {
-          const unsigned long long dk = (unsigned long long)((uint32_t)(key[k] >> 32) - dmin);
-          const unsigned long long kk =
-              ishift < 0 ? dk : ((dk << ishift) | (unsigned long long)((uint32_t)key[k] - imin));
-          d = (uint32_t)(kk >> (shift + lsb)) & 0xffu;
-        }
+        const uint32_t d = valid ? digit(key[k], shift) : 0u;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int bit = 0; bit < 8; bit++) {
