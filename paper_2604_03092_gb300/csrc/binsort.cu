@@ -381,29 +381,24 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
   const int per = (((n + NWARPS - 1) / NWARPS) + 31) & ~31;
   const int lo = min(wid * per, n), hi = min(lo + per, n);
   const int nr = (hi - lo + 31) >> 5;  // rounds of this warp (<= ITEMS)
+  const int passes = (nbits + 7) >> 3;
   unsigned long long* src = a;
   unsigned long long* dst = b;
-  if (nbits <= 0) return src;
-  auto digit = [&](unsigned long long key, int shift, uint32_t mask) -> uint32_t {
+  auto digit = [&](unsigned long long key, int shift) -> uint32_t {
     const unsigned long long dk = (unsigned long long)((uint32_t)(key >> 32) - dmin);
     const unsigned long long kk = ishift < 0 ? dk : ((dk << ishift) | (unsigned long long)((uint32_t)key - imin));
-    return (uint32_t)(kk >> (shift + lsb)) & mask;
+    return (uint32_t)(kk >> (shift + lsb)) & 0xffu;
   };
-  // ---- first pass: the lowest B1 bits, unstable -------------------------
-  // An LSD sort's first pass may leave equal digits in any order (the order
-  // it starts from is arbitrary): each key takes its slot within its digit
-  // from one shared atomic on a 2^B1-bin histogram held in the counter space,
-  // and the bins are scanned, at most four per thread.
-  constexpr int B1 = NWARPS >= 32 ? 12 : (NWARPS >= 16 ? 11 : 10);
-  static_assert((4u << B1) <= RegSortSmem<NWARPS>::CNT_BYTES, "the first pass's histogram fits the counter space");
-  static_assert((1 << B1) <= 4 * NT, "at most four bins per thread");
-  const int w1 = min(nbits, B1);
-  {
-    const int nb = 1 << w1, bpt = (nb + NT - 1) / NT;
-    uint32_t* hist = reinterpret_cast<uint32_t*>(cnt);
+  int first = 0;
+  if (passes > 0) {
+    // The first pass may leave equal digits in any order (the order it starts
+    // from is arbitrary anyway): each key takes its slot within its digit from
+    // one shared atomic on a 256-bin histogram, and only the 256 bins are
+    // scanned.  The later passes keep the order of equal digits (below).
+    uint32_t* hist = reinterpret_cast<uint32_t*>(cnt);  // 256 words of the counter space
     unsigned long long key[ITEMS];
     uint32_t off[ITEMS];
-    for (int i = threadIdx.x; i < nb; i += NT) hist[i] = 0u;
+    for (int i = threadIdx.x; i < 256; i += NT) hist[i] = 0u;
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
       const int i = lo + k * 32 + lane;
@@ -413,41 +408,27 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
       if (k < nr && lo + k * 32 + lane < hi) {
-        const uint32_t d = digit(key[k], 0, (uint32_t)nb - 1u);
+        const uint32_t d = digit(key[k], 0);
         off[k] = (d << 16) | atomicAdd(&hist[d], 1u);
       }
     }
     __syncthreads();
-    const int b0 = (int)threadIdx.x * bpt;
-    uint32_t c[4], sum = 0;
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      c[j] = (j < bpt && b0 + j < nb) ? hist[b0 + j] : 0u;
-      sum += c[j];
-    }
-    uint32_t x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      uint32_t y = lane < NWARPS ? tot[lane] : 0u;
+    uint32_t v = 0, x = 0;
+    if (threadIdx.x < 256) {
+      v = hist[threadIdx.x];
+      x = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-        if (lane >= o) y += z;
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      if (lane < NWARPS) tot[lane] = y;
+      if (lane == 31) tot[wid] = x;
     }
     __syncthreads();
-    uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
-#pragma unroll
-    for (int j = 0; j < 4; j++) {
-      if (j < bpt && b0 + j < nb) hist[b0 + j] = ex;
-      ex += c[j];
+    if (threadIdx.x < 256) {
+      uint32_t before = 0;
+      for (int w = 0; w < wid; w++) before += tot[w];
+      hist[threadIdx.x] = before + x - v;
     }
     __syncthreads();
 #pragma unroll
@@ -457,11 +438,10 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
     unsigned long long* t = src;
     src = dst;
     dst = t;
+    first = 1;
   }
-  // ---- later passes: up to 8 bits each, stable ---------------------------
-  for (int shift = w1; shift < nbits; shift += 8) {
-    const int wb = min(8, nbits - shift), nd = 1 << wb;
-    const int nth = nd * NWARPS / 8;  // threads of the counter scan, 8 counters each
+  for (int pass = first; pass < passes; pass++) {
+    const int shift = 8 * pass;
     unsigned long long key[ITEMS];
     uint32_t off[ITEMS];
 #pragma unroll
@@ -469,21 +449,19 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
       const int i = lo + k * 32 + lane;
       key[k] = (k < nr && i < hi) ? src[i] : 0ull;
     }
-    for (int i = threadIdx.x; i < nd * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
+    for (int i = threadIdx.x; i < 256 * CP / 2; i += NT) reinterpret_cast<uint32_t*>(cnt)[i] = 0u;
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
       if (k < nr) {
         const bool valid = lo + k * 32 + lane < hi;
-        const uint32_t d = valid ? digit(key[k], shift, (uint32_t)nd - 1u) : 0u;
+        const uint32_t d = valid ? digit(key[k], shift) : 0u;
         uint32_t peers = __ballot_sync(0xffffffffu, valid);
 #pragma unroll
         for (int bit = 0; bit < 8; bit++) {
-          if (bit < wb) {
-            const bool on = (d >> bit) & 1u;
-            const uint32_t bal = __ballot_sync(0xffffffffu, on);
-            peers &= on ? bal : ~bal;
-          }
+          const bool on = (d >> bit) & 1u;
+          const uint32_t bal = __ballot_sync(0xffffffffu, on);
+          peers &= on ? bal : ~bal;
         }
         const int leader = __ffs(peers) - 1;
         uint32_t pre = 0;
@@ -498,14 +476,12 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
     }
     __syncthreads();
     {
-      // exclusive scan of the nd * NWARPS counters in (digit, warp) order,
-      // 8 per thread over the first nth threads
-      const bool sc = (int)threadIdx.x < nth;
+      // exclusive scan of the counters in (digit, warp) order, 8 per thread
       const int f0 = 8 * threadIdx.x, d = f0 / NWARPS, w0 = f0 % NWARPS;
       uint32_t c[8], sum = 0;
 #pragma unroll
       for (int j = 0; j < 8; j++) {
-        c[j] = sc ? cnt[d * CP + w0 + j] : 0u;
+        c[j] = cnt[d * CP + w0 + j];
         sum += c[j];
       }
       uint32_t x = sum;
@@ -514,26 +490,23 @@ __device__ unsigned long long* block_radix_reg(unsigned long long* a, unsigned l
         const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      const int nws = (nth + 31) >> 5;  // warps of the scan
-      if (lane == 31 && wid < nws) tot[wid] = x;
+      if (lane == 31) tot[wid] = x;
       __syncthreads();
       if (wid == 0) {
-        uint32_t y = lane < nws ? tot[lane] : 0u;
+        uint32_t y = lane < NWARPS ? tot[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
           if (lane >= o) y += z;
         }
-        if (lane < nws) tot[lane] = y;
+        if (lane < NWARPS) tot[lane] = y;
       }
       __syncthreads();
-      if (sc) {
-        uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
+      uint32_t ex = x - sum + (wid > 0 ? tot[wid - 1] : 0u);
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          cnt[d * CP + w0 + j] = (uint16_t)ex;
-          ex += c[j];
-        }
+      for (int j = 0; j < 8; j++) {
+        cnt[d * CP + w0 + j] = (uint16_t)ex;
+        ex += c[j];
       }
     }
     __syncthreads();
