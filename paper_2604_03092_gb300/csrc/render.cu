@@ -234,6 +234,23 @@ __device__ __forceinline__ uint32_t lane_word(const SRecs<CHUNK>& s_rec, int wd,
   return cw & rw;
 }
 
+// Position of the r-th set bit (r >= 1, counted from bit 0) of a word that
+// has at least r set bits: a binary search on population counts of halves.
+__device__ __forceinline__ int nth_set_bit(uint32_t b, int r) {
+  int pos = 0, c;
+  c = __popc(b & 0xffffu);
+  if (r > c) { r -= c; b >>= 16; pos += 16; }
+  c = __popc(b & 0xffu);
+  if (r > c) { r -= c; b >>= 8; pos += 8; }
+  c = __popc(b & 0xfu);
+  if (r > c) { r -= c; b >>= 4; pos += 4; }
+  c = __popc(b & 0x3u);
+  if (r > c) { r -= c; b >>= 2; pos += 2; }
+  c = (int)(b & 1u);
+  if (r > c) pos += 1;
+  return pos;
+}
+
 // Sum 8 per-lane values over the warp and give every lane all 8 totals
 // (a transposing butterfly: each level halves the values a lane keeps).
 __device__ __forceinline__ void warp_sum8_all(float (&v)[8], int lane) {
@@ -834,9 +851,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
             if (c0 > q) { wd = 2 * h; cin = c0; }
             if (c1 > q) { wd = 2 * h + 1; cin = c1; }
           }
-          // the (cin - q)-th set bit of the word from bit 0 (it exists: cin - q
-          // <= the word's set bits); clamped into the chunk all the same
-          j = min(max(wd * 32 + (int)__fns(S.pbits[ps][wd], 0u, cin - q), 0), CHUNK - 1);
+          j = wd * 32 + nth_set_bit(S.pbits[ps][wd], cin - q);
         }
         const bool start = has && (lane == 0 || ((M >> lane) & 1u));
         const bool end = has && (lane == 31 || base + lane + 1 == total || ((M >> (lane + 1)) & 1u));
