@@ -29,9 +29,9 @@ CANDIDATES: List[Candidate] = [(16, 16, 256, 256), (16, 16, 128, 128), (16, 16, 
 # keyframe seen from 8 views (img18_dens0), 64 uneven submaps at
 # 320x240..640x480 (img18_dens1: 8x8/64/64 91.8 ms, 8x8/128/64 93.2 ms),
 # 8- and 32-keyframe submaps at 512x384 (img18_dens3, img18_dens5:
-# 8x8/64/64 70.3 ms, 8x8/128/64 72.0 ms, 16x16/256/256 107.9 ms), the
-# 150-keyframe map seen at 640x480 (img18_dens7: 8x8/64/64 64.7 ms,
-# 8x8/128/64 65.6 ms, 16x16/256/256 85.5 ms).
+# 8x8/64/64 66.8 ms, 8x8/128/64 68.2 ms, 16x16/256/256 102.1 ms), the
+# 150-keyframe map seen at 640x480 (img18_dens7: 8x8/64/64 59.7 ms,
+# 8x8/128/64 60.4 ms, 16x16/256/256 79.6 ms).
 SHIPPED: Dict[str, Candidate] = {"img18_dens0": (8, 8, 128, 64), "img18_dens1": (8, 8, 64, 64),
                                  "img18_dens3": (8, 8, 64, 64), "img18_dens5": (8, 8, 64, 64),
                                  "img18_dens7": (8, 8, 64, 64)}
