@@ -928,32 +928,35 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         if (P.depth_ray) pair_grads_ray_depth(e, qj, col.w, zp, w * u0.w + dzd, g, gz);
         if (kept) {
           float* sg = S.grad + j * SGRAD_STRIDE;
-          [[maybe_unused]] uint32_t outside = 0u;  // fixed point: terms outside the chunk's range
+          [[maybe_unused]] float umax = 0.f;  // fixed point: the largest scaled term
 #pragma unroll
           for (int q = 0; q < SGRAD_STRIDE; q++) {
             if (!want_n && q >= G_NX && q <= G_NZ) continue;  // no normal gradient requested
             const float t = q < 16 ? g[q] : gz;
             if constexpr (FIXED) {
-              // no scale yet (+inf) makes u infinite or NaN: the term goes outside.
-              // Branch-free: a term outside this chunk's range adds zero here
-              // and is marked; the marked terms go to global memory below.
+              // no scale yet (+inf) makes u infinite (or NaN for t = 0).
+              // Branch-free: a term outside this chunk's range adds zero here;
+              // the pair's largest |u| tells whether any did (fmaxf drops NaN).
               const uint32_t w2 = gexp[q >> 1];
               const float u = t * __uint_as_float((q & 1) ? (w2 & 0xffff0000u) : (w2 << 16));
               const bool in = fabsf(u) < FIX_LIMIT;
               atomicAdd(reinterpret_cast<int*>(sg + q),
                         __float_as_int(__fadd_rn(in ? u : 0.f, FIX_MAGIC)) - FIX_MAGIC_BITS);
-              outside |= (!in && t != 0.f) ? (1u << q) : 0u;
+              umax = fmaxf(umax, fabsf(u));
             } else {
               if (t != 0.f) atomicAdd(sg + q, t);
             }
           }
           if constexpr (FIXED) {
-            if (outside) {  // outside this chunk's range (or not finite): added exactly
+            if (!(umax < FIX_LIMIT)) {  // some term outside this chunk's range (or not finite): added exactly
               float* dst = A.rgrad + (int64_t)S.idx[j] * GRAD_F;
 #pragma unroll
               for (int q = 0; q < SGRAD_STRIDE; q++) {
-                if (!((outside >> q) & 1u)) continue;
+                if (!want_n && q >= G_NX && q <= G_NZ) continue;
                 const float t = q < 16 ? g[q] : gz;
+                const uint32_t w2 = gexp[q >> 1];
+                const float u = t * __uint_as_float((q & 1) ? (w2 & 0xffff0000u) : (w2 << 16));
+                if (fabsf(u) < FIX_LIMIT || t == 0.f) continue;
                 atomicAdd(dst + q, t);
                 atomicMax(&S.ofl[q], (__float_as_uint(t) >> 23) & 0xffu);
                 n_outside++;
