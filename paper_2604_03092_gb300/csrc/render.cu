@@ -387,14 +387,10 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
         }
         for (int wd = 0; wd < nwd; wd++) S.bits[wid][wd][lane] = lane_word(S.rec, wd, count, bx - tx0, by - ty0, lane);
         int wd = 0;
-        uint32_t b = S.bits[wid][0][lane];  // a lane done already keeps its bits and takes none of them
+        uint32_t b = done ? 0u : S.bits[wid][0][lane];
         uint32_t bl = 0u;  // entries of word wd this pixel blended (word wd's slot takes them when the walk moves on)
-        // the pair counters come from the masks, per word: evaluated = the
-        // word's in-rect entries taken, blended = its blended entries
         for (;;) {
           while (b == 0 && !done && wd + 1 < nwd) {
-            n_eval += __popc(S.bits[wid][wd][lane]);
-            n_blend += __popc(bl);
             S.bits[wid][wd][lane] = bl;
             bl = 0u;
             b = S.bits[wid][++wd][lane];
@@ -406,6 +402,7 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           b &= b - 1;
           Pair e;
           eval_pair(S.rec.c[j], S.rec.p[j], S.rec.q[j], px, py, P.lp_scale, P.alpha_max, e);
+          n_eval++;
           if (e.alpha < P.alpha_min) continue;
           const float Tn = __fmul_rn(T, __fsub_rn(1.f, e.alpha));
           if (Tn < P.t_min) {
@@ -427,9 +424,8 @@ __global__ void __launch_bounds__(TW* TH, (TW * TH == 64) ? (CHUNK <= 64 ? 16 : 
           T = Tn;
           last = (uint32_t)(base + j + 1);
           bl |= 1u << (j & 31);
+          n_blend++;
         }
-        n_eval += __popc(S.bits[wid][wd][lane]) - __popc(b);  // the entries left in b were not taken
-        n_blend += __popc(bl);
         S.bits[wid][wd][lane] = bl;
         for (int w2 = wd + 1; w2 < nwd; w2++) S.bits[wid][w2][lane] = 0u;
         uint32_t* bm = A.bmask + (size_t)mask_word() * NT + threadIdx.x;
