@@ -108,6 +108,8 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
       d.W = sv.width;
       d.H = sv.height;
       d.fx = sv.fx; d.fy = sv.fy; d.cx = sv.cx; d.cy = sv.cy;
+      d.ifx = 1.0f / sv.fx;  // the same correctly rounded quotient the kernels took per pair
+      d.ify = 1.0f / sv.fy;
       for (int r = 0; r < 3; r++) {
         for (int c = 0; c < 3; c++) d.R[r * 3 + c] = sv.Rt[r * 4 + c];
         d.t[r] = sv.Rt[r * 4 + 3];

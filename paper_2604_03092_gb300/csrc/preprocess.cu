@@ -60,6 +60,7 @@ struct Surfel {
   float qh[4], qn;          // normalised quaternion and the norm of the input
   float tu[3], tv[3], nw[3];  // columns of R(q)
   float op;
+  float k2, kk;  // 2 ln(op / alpha_min) and its square root (per surfel, for every view)
   bool valid;
 };
 
@@ -164,8 +165,7 @@ __device__ __forceinline__ uint32_t project_one(const PreArgs& A, const DView& v
   if (dot3(nc, mc) > 0.f) {
     nc[0] = -nc[0]; nc[1] = -nc[1]; nc[2] = -nc[2];
   }
-  const float k2 = 2.0f * logf(f.op / P.alpha_min);
-  const float kk = sqrtf(k2);
+  const float k2 = f.k2, kk = f.kk;
   const float zmin = mzh - kk * sqrtf(U[2] * U[2] + V[2] * V[2]);
   if (!(zmin > P.z_near)) return 0;
 
@@ -229,7 +229,7 @@ __device__ __forceinline__ uint32_t project_one(const PreArgs& A, const DView& v
   if (nn > 0.f && isfinite(nn)) {
     const float iN = 1.0f / nn;
     const float sk = 0.84932180028801907f;  // sqrt(log2(e) / 2)
-    const float ifx = 1.0f / vw.fx, ify = 1.0f / vw.fy;
+    const float ifx = vw.ifx, ify = vw.ify;
     p00 = sk * av[0] * ifx * iN;
     p01 = sk * av[1] * ify * iN;
     p10 = sk * bv[0] * ifx * iN;
@@ -257,6 +257,9 @@ __global__ void __launch_bounds__(256, 3) k_preprocess(const PreArgs A) {
     const int64_t s = grp.soff + (w - grp.wbase);
     Surfel f;
     load_surfel(A.S, s, f);
+    // the extent's k^2 = 2 ln(op / alpha_min): the surfel's, whatever the view
+    f.k2 = 2.0f * logf(f.op / A.P.alpha_min);
+    f.kk = sqrtf(f.k2);
     const float cr = __ldg(A.S.rgb + 3 * s + 0), cg = __ldg(A.S.rgb + 3 * s + 1), cb = __ldg(A.S.rgb + 3 * s + 2);
     for (int v = grp.v0; v < grp.v1; v++) {
       const DView& vw = A.views[v];
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess_bwd(const PreBwdArgs A) {
           float gU[3] = {0.f, 0.f, 0.f}, gV[3] = {0.f, 0.f, 0.f}, gmc[3] = {0.f, 0.f, 0.f};
           if (nn > 0.f && isfinite(nn)) {
             const float iN = 1.0f / nn;
-            const float ifx = 1.0f / vw.fx, ify = 1.0f / vw.fy;
+            const float ifx = vw.ifx, ify = vw.ify;
             // d/d(rows of adj): the normalisation carries no gradient
             float ga[3] = {gr[G_P00] * sk * ifx * iN, gr[G_P01] * sk * ify * iN, 0.f};
             float gb[3] = {gr[G_P10] * sk * ifx * iN, gr[G_P11] * sk * ify * iN, 0.f};

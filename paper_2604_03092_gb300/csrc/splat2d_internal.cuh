@@ -29,7 +29,7 @@ struct DView {
   int32_t tile_base;  // first global tile of this view
   int32_t tiles_x, tiles_y;
   int32_t group;
-  int32_t pad[2];
+  float ifx, ify;  // 1 / fx and 1 / fy, IEEE quotients computed on the host
 };
 static_assert(sizeof(DView) == 128, "DView layout");
 
