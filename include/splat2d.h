@@ -140,7 +140,7 @@ typedef struct {
 #define SPLAT2D_FLAG_DEPTH_RAY 2u
 /* Bits 8..15 of flags: forward tail threshold, pixels per warp of a tile below
  * which the forward shares the tile's remaining pixels across all warps
- * (0 = the default of 8; 255 = always).  A launch-shape knob for the
+ * (0 = the default of 6; 255 = always).  A launch-shape knob for the
  * autotuner: it changes the schedule, not the result beyond rounding. */
 #define SPLAT2D_FLAG_TAIL_SHIFT 8
 

@@ -202,7 +202,7 @@ static RastParams make_params(const splat2d_config* c) {
   P.stats = (c->flags & SPLAT2D_FLAG_NO_STATS) ? 0 : 1;
   P.depth_ray = (c->flags & SPLAT2D_FLAG_DEPTH_RAY) ? 1 : 0;
   const int tail = (int)((c->flags >> SPLAT2D_FLAG_TAIL_SHIFT) & 0xffu);
-  P.fwd_tail = tail == 0 ? 8 : (tail == 255 ? 1 << 20 : tail);
+  P.fwd_tail = tail == 0 ? 6 : (tail == 255 ? 1 << 20 : tail);
   return P;
 }
 
