@@ -362,7 +362,9 @@ __device__ void sort_bucket_any(unsigned long long* a, unsigned long long* b, in
 // of the (digit, warp) counters in digit-major order turns them into output
 // offsets, so equal digits keep their order (stable), and every key is then
 // stored at its offset.  Digits are those of block_radix_any.  Returns the
-// buffer holding the result (a or b).
+// buffer holding the result (a or b).  a and b may be the same buffer: a
+// pass loads all its keys into registers before a block barrier and
+// scatters them after it.
 template <int NWARPS>
 struct RegSortSmem {
   static constexpr int CP = NWARPS + 2;  // padded counter row: conflict-free leader updates
@@ -627,22 +629,26 @@ template <int NWARPS, int ITEMS>
 struct SegClass {
   static constexpr int THREADS = NWARPS * 32;
   static constexpr int CAP = NWARPS * 32 * ITEMS;
-  static constexpr size_t SMEM = 2 * sizeof(unsigned long long) * CAP + RegSortSmem<NWARPS>::BYTES;
-  static_assert(2 * sizeof(unsigned long long) * CAP >= sizeof(uint32_t) * ((NWARPS + 1) * 256 + 8),
-                "the oversized-bucket counters fit in the key buffers");
+  static constexpr size_t SMEM = sizeof(unsigned long long) * CAP + RegSortSmem<NWARPS>::BYTES;
 };
 
 template <int NWARPS, int ITEMS, bool LAST>
-// The 1025..4096 class (74.9 KB of shared memory) runs 3 CTAs per SM under
-// a 42-register bound: its keys spill, but the third CTA hides more of the
-// barrier waits (binning 10.01 -> 9.82 ms on the 32-keyframe submap).
-__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? (ITEMS <= 8 ? 3 : 2) : 1) k_tile_sort(const SegArgs A) {
+// The bucket is sorted in place in one shared buffer (each radix pass holds
+// its keys in registers between its loads and its scatter, with block
+// barriers in between), so the 1025..4096 and 4097..6144 classes (41 KB and
+// 57 KB of shared memory) run 3 CTAs per SM under a 42-register bound: their
+// keys spill, but the third CTA hides more of the barrier waits (binning
+// 10.01 -> 9.82 ms for the first class, 9.82 -> 9.62 ms for the second, on
+// the 32-keyframe submap).
+__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : 1) k_tile_sort(const SegArgs A) {
   using C = SegClass<NWARPS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* sa = reinterpret_cast<unsigned long long*>(smem);
-  unsigned long long* sb = sa + C::CAP;
-  uint16_t* cnt = reinterpret_cast<uint16_t*>(sb + C::CAP);
-  uint32_t* tot = reinterpret_cast<uint32_t*>(smem + 2 * sizeof(unsigned long long) * C::CAP +
+  unsigned long long* sb = sa;  // in place: every pass holds its keys in registers
+  static_assert(!LAST || sizeof(unsigned long long) * C::CAP >= sizeof(uint32_t) * ((NWARPS + 1) * 256 + 8),
+                "the oversized-bucket counters fit in the key buffer");
+  uint16_t* cnt = reinterpret_cast<uint16_t*>(sa + C::CAP);
+  uint32_t* tot = reinterpret_cast<uint32_t*>(smem + sizeof(unsigned long long) * C::CAP +
                                               ((RegSortSmem<NWARPS>::CNT_BYTES + 15) & ~(size_t)15));
   uint32_t* red = tot + 32;
   __shared__ uint32_t s_q;
