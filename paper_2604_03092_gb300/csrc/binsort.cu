@@ -639,8 +639,10 @@ template <int NWARPS, int ITEMS, bool LAST>
 // 57 KB of shared memory) run 3 CTAs per SM under a 42-register bound: their
 // keys spill, but the third CTA hides more of the barrier waits (binning
 // 10.01 -> 9.82 ms for the first class, 9.82 -> 9.62 ms for the second, on
-// the 32-keyframe submap).
-__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : 1) k_tile_sort(const SegArgs A) {
+// the 32-keyframe submap).  The <= 1024 class (13 KB) runs 6 CTAs per SM,
+// which matters where buckets are short (64 uneven submaps: binning 13.38 ->
+// 11.37 ms).
+__global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : (NWARPS == 8 ? 6 : 1)) k_tile_sort(const SegArgs A) {
   using C = SegClass<NWARPS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* sa = reinterpret_cast<unsigned long long*>(smem);
