@@ -128,13 +128,14 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
 
 // Size classes of the per-tile bucket sorts (upper bounds, inclusive; longer
 // buckets go with the last class).
-constexpr int SORT_CLASSES = 4;
-constexpr int SORT_CLASS_BOUND[SORT_CLASSES] = {1024, 4096, 6144, 12288};
+constexpr int SORT_CLASSES = 5;
+constexpr int SORT_CLASS_BOUND[SORT_CLASSES] = {1024, 4096, 6144, 8192, 12288};
 
 __device__ __forceinline__ int sort_class(uint32_t n) {
-  static_assert(SORT_CLASSES == 4, "one comparison per class bound");
-  constexpr uint32_t b0 = SORT_CLASS_BOUND[0], b1 = SORT_CLASS_BOUND[1], b2 = SORT_CLASS_BOUND[2];
-  return n == 0 ? -1 : (n <= b0 ? 0 : (n <= b1 ? 1 : (n <= b2 ? 2 : 3)));
+  static_assert(SORT_CLASSES == 5, "one comparison per class bound");
+  constexpr uint32_t b0 = SORT_CLASS_BOUND[0], b1 = SORT_CLASS_BOUND[1], b2 = SORT_CLASS_BOUND[2],
+                     b3 = SORT_CLASS_BOUND[3];
+  return n == 0 ? -1 : (n <= b0 ? 0 : (n <= b1 ? 1 : (n <= b2 ? 2 : (n <= b3 ? 3 : 4))));
 }
 
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
@@ -635,13 +636,15 @@ struct SegClass {
 template <int NWARPS, int ITEMS, bool LAST>
 // The bucket is sorted in place in one shared buffer (each radix pass holds
 // its keys in registers between its loads and its scatter, with block
-// barriers in between), so the 1025..4096 and 4097..6144 classes (41 KB and
-// 57 KB of shared memory) run 3 CTAs per SM under a 42-register bound: their
-// keys spill, but the third CTA hides more of the barrier waits (binning
-// 10.01 -> 9.82 ms for the first class, 9.82 -> 9.62 ms for the second, on
-// the 32-keyframe submap).  The <= 1024 class (13 KB) runs 6 CTAs per SM,
-// which matters where buckets are short (64 uneven submaps: binning 13.38 ->
-// 11.37 ms).
+// barriers in between), so the 1025..4096, 4097..6144 and 6145..8192 classes
+// (41, 57 and 73 KB of shared memory) run 3 CTAs per SM under a 42-register
+// bound: their keys spill, but the third CTA hides more of the barrier waits
+// (binning 10.01 -> 9.82 ms for the first class, 9.82 -> 9.62 ms for the
+// second, on the 32-keyframe submap; sorting the 6145..8192 buckets there
+// instead of in the 1024-thread class at one CTA per SM: 9.63 -> 9.37 ms, and
+// 9.46 ms at 2 CTAs per SM without the spills).  The <= 1024 class (13 KB)
+// runs 6 CTAs per SM, which matters where buckets are short (64 uneven
+// submaps: binning 13.38 -> 11.37 ms).
 __global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : (NWARPS == 8 ? 6 : 1)) k_tile_sort(const SegArgs A) {
   using C = SegClass<NWARPS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -739,7 +742,8 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   S.hdr = hdr;
   S.cap = L.cap;
   static_assert(SegClass<8, 4>::CAP == SORT_CLASS_BOUND[0] && SegClass<16, 8>::CAP == SORT_CLASS_BOUND[1] &&
-                    SegClass<16, 12>::CAP == SORT_CLASS_BOUND[2] && SegClass<32, 12>::CAP == SORT_CLASS_BOUND[3],
+                    SegClass<16, 12>::CAP == SORT_CLASS_BOUND[2] && SegClass<16, 16>::CAP == SORT_CLASS_BOUND[3] &&
+                    SegClass<32, 12>::CAP == SORT_CLASS_BOUND[4],
                 "class capacities match the class bounds");
   for (int c = 0; c < SORT_CLASSES; c++) {
     S.list = class_list + (size_t)c * L.T;
@@ -749,6 +753,7 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
       case 0: e = launch_tile_sort_class<8, 4, false>(S, st); break;
       case 1: e = launch_tile_sort_class<16, 8, false>(S, st); break;
       case 2: e = launch_tile_sort_class<16, 12, false>(S, st); break;
+      case 3: e = launch_tile_sort_class<16, 16, false>(S, st); break;
       default: e = launch_tile_sort_class<32, 12, true>(S, st); break;
     }
     if (e != cudaSuccess) return e;
