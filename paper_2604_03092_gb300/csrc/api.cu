@@ -166,7 +166,7 @@ static bool build_tables(const splat2d_config* cfg, const splat2d_problem* prob,
   L->tile_cursor = take(sizeof(uint32_t) * T);  // scatter cursors (from the tile scan)
   L->tile_order = take(sizeof(uint32_t) * T);
   L->tile_hist = take(sizeof(uint32_t) * (ORDER_BINS + 16));
-  L->tile_class = take(sizeof(uint32_t) * 5 * (size_t)T);  // one list per bucket-sort size class
+  L->tile_class = take(sizeof(uint32_t) * 6 * (size_t)T);  // one list per bucket-sort size class
   L->tfinal = take(sizeof(float) * P);
   L->last = take(sizeof(uint32_t) * P);
   L->dfinal = take(sizeof(float) * P);  // per pixel: the depth sum D (the depth-distortion adjoint needs it)

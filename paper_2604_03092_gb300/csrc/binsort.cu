@@ -128,14 +128,15 @@ __global__ void __launch_bounds__(256) k_tile_bin(const TileBinArgs A) {
 
 // Size classes of the per-tile bucket sorts (upper bounds, inclusive; longer
 // buckets go with the last class).
-constexpr int SORT_CLASSES = 5;
-constexpr int SORT_CLASS_BOUND[SORT_CLASSES] = {1024, 4096, 6144, 8192, 12288};
+constexpr int SORT_CLASSES = 6;
+constexpr int SORT_CLASS_BOUND[SORT_CLASSES] = {1024, 2048, 4096, 6144, 8192, 12288};
 
 __device__ __forceinline__ int sort_class(uint32_t n) {
-  static_assert(SORT_CLASSES == 5, "one comparison per class bound");
+  static_assert(SORT_CLASSES == 6, "one comparison per class bound");
   constexpr uint32_t b0 = SORT_CLASS_BOUND[0], b1 = SORT_CLASS_BOUND[1], b2 = SORT_CLASS_BOUND[2],
-                     b3 = SORT_CLASS_BOUND[3];
-  return n == 0 ? -1 : (n <= b0 ? 0 : (n <= b1 ? 1 : (n <= b2 ? 2 : (n <= b3 ? 3 : 4))));
+                     b3 = SORT_CLASS_BOUND[3], b4 = SORT_CLASS_BOUND[4];
+  return n == 0 ? -1
+                : (n <= b0 ? 0 : (n <= b1 ? 1 : (n <= b2 ? 2 : (n <= b3 ? 3 : (n <= b4 ? 4 : 5)))));
 }
 
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
@@ -642,9 +643,11 @@ template <int NWARPS, int ITEMS, bool LAST>
 // (binning 10.01 -> 9.82 ms for the first class, 9.82 -> 9.62 ms for the
 // second, on the 32-keyframe submap; sorting the 6145..8192 buckets there
 // instead of in the 1024-thread class at one CTA per SM: 9.63 -> 9.37 ms, and
-// 9.46 ms at 2 CTAs per SM without the spills).  The <= 1024 class (13 KB)
-// runs 6 CTAs per SM, which matters where buckets are short (64 uneven
-// submaps: binning 13.38 -> 11.37 ms).
+// 9.46 ms at 2 CTAs per SM without the spills).  The <= 1024 and 1025..2048
+// classes (256 threads, 13 and 21 KB) run 6 CTAs per SM, which matters where
+// buckets are short (64 uneven submaps: binning 13.38 -> 11.37 ms for the
+// first, and 11.62 -> 11.35 ms for taking the 1025..2048 buckets out of the
+// 512-thread class).
 __global__ void __launch_bounds__(NWARPS * 32, NWARPS == 16 ? 3 : (NWARPS == 8 ? 6 : 1)) k_tile_sort(const SegArgs A) {
   using C = SegClass<NWARPS, ITEMS>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -741,9 +744,9 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
   S.vals = reinterpret_cast<uint32_t*>(ws + L.vals0);
   S.hdr = hdr;
   S.cap = L.cap;
-  static_assert(SegClass<8, 4>::CAP == SORT_CLASS_BOUND[0] && SegClass<16, 8>::CAP == SORT_CLASS_BOUND[1] &&
-                    SegClass<16, 12>::CAP == SORT_CLASS_BOUND[2] && SegClass<16, 16>::CAP == SORT_CLASS_BOUND[3] &&
-                    SegClass<32, 12>::CAP == SORT_CLASS_BOUND[4],
+  static_assert(SegClass<8, 4>::CAP == SORT_CLASS_BOUND[0] && SegClass<8, 8>::CAP == SORT_CLASS_BOUND[1] &&
+                    SegClass<16, 8>::CAP == SORT_CLASS_BOUND[2] && SegClass<16, 12>::CAP == SORT_CLASS_BOUND[3] &&
+                    SegClass<16, 16>::CAP == SORT_CLASS_BOUND[4] && SegClass<32, 12>::CAP == SORT_CLASS_BOUND[5],
                 "class capacities match the class bounds");
   for (int c = 0; c < SORT_CLASSES; c++) {
     S.list = class_list + (size_t)c * L.T;
@@ -751,9 +754,10 @@ cudaError_t launch_bin_tiles(const Layout& L, const RastParams& P, char* ws, cud
     S.queue = queues + c;
     switch (c) {
       case 0: e = launch_tile_sort_class<8, 4, false>(S, st); break;
-      case 1: e = launch_tile_sort_class<16, 8, false>(S, st); break;
-      case 2: e = launch_tile_sort_class<16, 12, false>(S, st); break;
-      case 3: e = launch_tile_sort_class<16, 16, false>(S, st); break;
+      case 1: e = launch_tile_sort_class<8, 8, false>(S, st); break;
+      case 2: e = launch_tile_sort_class<16, 8, false>(S, st); break;
+      case 3: e = launch_tile_sort_class<16, 12, false>(S, st); break;
+      case 4: e = launch_tile_sort_class<16, 16, false>(S, st); break;
       default: e = launch_tile_sort_class<32, 12, true>(S, st); break;
     }
     if (e != cudaSuccess) return e;

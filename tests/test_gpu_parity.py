@@ -181,16 +181,18 @@ def test_bin_sort_runs_again_on_one_preprocess():
 def test_bin_sort_long_buckets_and_equal_depths(n, tile):
     # every surfel covers the image centre, so the central tiles hold close to
     # n entries: the per-tile sort runs its middle and large size classes (at
-    # n = 9000 the 16x16 tiles hold about 7600 and 8900 entries, one bucket
-    # each side of 8192) and, above 12288 entries, its global-memory path;
-    # half of the surfels share one depth exactly (identity pose: the depth
-    # key is the centre's z), so the buckets hold runs of equal depth far
-    # longer than 64
+    # n = 2500 the 16x16 tiles hold 1038..2472 entries, either side of 2048;
+    # at n = 9000 about 7600 and 8900, either side of 8192) and, above 12288
+    # entries, its global-memory path; half of the surfels share one depth
+    # exactly (identity pose: the depth key is the centre's z), so the
+    # buckets hold runs of equal depth far longer than 64
     sc = scenes.random_scene(n=n, width=64, height=48, f=60.0, seed=11, xy_range=0.3, scale_range=(0.2, 0.5),
                              n_views=1, with_target=False)
     sc.means[::2, 2] = np.float32(3.0)
     counts = _check_bin_sort(sc, tile)
     assert counts.max() > {2500: 1024, 9000: 8192, 30000: 12288}[n]
+    if n == 2500:
+        assert ((counts > 1024) & (counts <= 2048)).any()
     if n == 9000:
         assert ((counts > 6144) & (counts <= 8192)).any()
 
