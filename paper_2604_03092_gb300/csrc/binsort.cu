@@ -141,7 +141,10 @@ __device__ __forceinline__ int sort_class(uint32_t n) {
 
 // One block: exclusive scan of the tile counts -> ranges, scatter cursors,
 // total and the capacity check; every non-empty tile is appended to the list
-// of its sort size class.
+// of its sort size class.  Each thread takes SCAN_ITEMS consecutive tiles per
+// sweep, so a sweep covers 8192 tiles with one block-wide scan of the
+// threads' sums (a 64-view batch of about 770 K tiles takes 95 sweeps).
+constexpr int SCAN_ITEMS = 8;
 
 __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__ counts,
                                                     uint32_t* __restrict__ cursors, uint2* __restrict__ ranges,
@@ -154,10 +157,16 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
-  for (int64_t base = 0; base < T; base += 1024) {
-    const int64_t i = base + threadIdx.x;
-    const unsigned long long v = i < T ? counts[i] : 0ull;
-    unsigned long long x = v;
+  for (int64_t base = 0; base < T; base += 1024 * SCAN_ITEMS) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+      v[j] = i0 + j < T ? counts[i0 + j] : 0u;
+      sum += v[j];
+    }
+    unsigned long long x = sum;
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -173,23 +182,28 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const uint32_t* __restrict__
       s_w[lane] = w;
     }
     __syncthreads();
-    const unsigned long long incl = x + (wid > 0 ? s_w[wid - 1] : 0ull) + s_carry;
-    const unsigned long long start = incl - v;
-    const bool fits = incl <= (unsigned long long)cap;
-    if (i < T) {
-      ranges[i] = fits ? make_uint2((uint32_t)start, (uint32_t)incl) : make_uint2(0u, 0u);
-      cursors[i] = fits ? (uint32_t)start : 0u;
-    }
-    // append the tile to its size class's list (order within a list is free)
-    const int cls = (i < T && fits) ? sort_class((uint32_t)v) : -1;
+    unsigned long long incl = x - sum + (wid > 0 ? s_w[wid - 1] : 0ull) + s_carry;
 #pragma unroll
-    for (int c = 0; c < SORT_CLASSES; c++) {
-      const uint32_t m = __ballot_sync(0xffffffffu, cls == c);
-      if (!m) continue;
-      uint32_t at = 0;
-      if (lane == 0) at = atomicAdd(&class_count[c], (uint32_t)__popc(m));
-      at = __shfl_sync(0xffffffffu, at, 0);
-      if (cls == c) class_list[(size_t)c * T + at + __popc(m & lt_mask)] = (uint32_t)i;
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+      const int64_t i = i0 + j;
+      const unsigned long long start = incl;
+      incl += v[j];
+      const bool fits = incl <= (unsigned long long)cap;
+      if (i < T) {
+        ranges[i] = fits ? make_uint2((uint32_t)start, (uint32_t)incl) : make_uint2(0u, 0u);
+        cursors[i] = fits ? (uint32_t)start : 0u;
+      }
+      // append the tile to its size class's list (order within a list is free)
+      const int cls = (i < T && fits) ? sort_class(v[j]) : -1;
+#pragma unroll
+      for (int c = 0; c < SORT_CLASSES; c++) {
+        const uint32_t m = __ballot_sync(0xffffffffu, cls == c);
+        if (!m) continue;
+        uint32_t at = 0;
+        if (lane == 0) at = atomicAdd(&class_count[c], (uint32_t)__popc(m));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (cls == c) class_list[(size_t)c * T + at + __popc(m & lt_mask)] = (uint32_t)i;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = incl;
